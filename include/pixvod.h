@@ -1,0 +1,211 @@
+/*
+ * pixvod.h - C ABI of the GB300 (sm_103a) PixVOD GBP sweep library.
+ *
+ * PixVOD (Kim, Alzugaray, Rhodes, Kelly, Davison; arxiv 2606.03989) tracks the
+ * 6-DoF motion of a camera relative to a keyframe and the keyframe's log-depth
+ * with synchronous Gaussian Belief Propagation over the pixel grid. Every pixel
+ * holds a 7-D belief (se(3) pose [theta; rho] and log-depth) in information form
+ * (Sec. 3.3, Sec. 3.4); factors are the photometric factor (Eq. 3, warp of Eq. 2,
+ * Huber by covariance weighting, Sec. 4.1), a pose prior (Eq. 4), a log-depth
+ * prior (Sec. 3.3), camera-motion identity factors between 4-neighbours (Eq. 5,
+ * grid pattern) and normal-integration factors between 4-neighbours (Eq. 6).
+ * One sweep linearises every factor at the current means, sends all
+ * factor-to-variable messages at once, damps them, updates the beliefs and
+ * moves the linearisation point, projecting stored messages onto the new
+ * tangent space (Sec. 4.1). A frame's pose is the pixel average of the pose
+ * components (App. C.2, estimator equation); keyframes are re-anchored by a
+ * count rule (Sec. 3.5, App. A).
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are device pointers (CUDA global memory of the device
+ *    that was current when the handle was created); h_* and plain arrays are
+ *    host pointers. The library never takes ownership of caller memory.
+ *  - Images are row-major, width x height, no padding, float32.
+ *  - Work is enqueued on the handle's stream; only calls documented as
+ *    synchronising wait for it. Device input buffers must stay valid and
+ *    unmodified until the enqueued work has consumed them.
+ *  - The library allocates no device memory: all device state lives in the
+ *    caller-provided workspace. It launches only its own kernels and plain
+ *    cudaMemcpyAsync / cudaMemsetAsync on the handle's stream.
+ *  - A handle is not thread-safe; use one handle per host thread or serialise.
+ *  - Errors: calls return a pixvod_status. PIXVOD_EINVAL leaves the handle
+ *    unchanged. PIXVOD_ECUDA reports a CUDA runtime error (the handle may then
+ *    be unusable). Numerical trouble inside kernels never traps: it sets sticky
+ *    flags read by pixvod_get_status.
+ */
+#ifndef PIXVOD_H
+#define PIXVOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIXVOD_ABI_VERSION 1
+
+typedef enum {
+    PIXVOD_OK = 0,
+    PIXVOD_EINVAL = 1,   /* bad argument: null or misaligned pointer, bad size, sigma <= 0 ... */
+    PIXVOD_ECUDA = 2,    /* a CUDA runtime call failed */
+    PIXVOD_ENUMERIC = 3, /* device flags report a numerical failure (see flags below) */
+    PIXVOD_ESTATE = 4,   /* call not valid in the handle's current state */
+    PIXVOD_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+    PIXVOD_ENOMEM = 6    /* workspace smaller than pixvod_workspace_bytes */
+} pixvod_status;
+
+/* Sticky device flags (bitwise OR), read with pixvod_get_status. */
+#define PIXVOD_FLAG_NONPOS_PIVOT 0x1u /* a Cholesky pivot was <= 0; that pixel skipped its update */
+#define PIXVOD_FLAG_NONFINITE    0x2u /* a non-finite mean was produced */
+#define PIXVOD_FLAG_TIMEOUT      0x4u /* a bounded spin-wait gave up */
+
+/* Pinhole intrinsics (Eq. 2): pixel centres at integer coordinates. */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} pixvod_intrinsics;
+
+/* Factor strengths and schedule. Each sigma enters as Lambda = I / sigma^2
+ * (Sec. 4.2). Defaults (pixvod_params_default): the paper's leaf values
+ * sigma_D = 5e-3, sigma_P = 1, sigma_R = 4e-4, sigma_N = 1e-3, t_huber = 400
+ * (Sec. 4.2); sigma_Z = 1 (log-depth prior, not given by the paper);
+ * damping = 0.5 (pairwise message damping, not in the paper); kf_interval = 10
+ * (frames per keyframe segment; the paper uses 150-300 on its 10x-upsampled
+ * sequences, App. A); precision = 32. */
+typedef struct {
+    float sigma_D;     /* photometric noise (intensities in [0, 1]) */
+    float sigma_P;     /* pose prior */
+    float sigma_R;     /* camera-motion identity factor */
+    float sigma_N;     /* normal-integration factor */
+    float sigma_Z;     /* log-depth prior */
+    float t_huber;     /* Huber threshold on |r| / sigma_D */
+    float damping;     /* beta in m <- (1 - beta) m_new + beta m_old, in [0, 1) */
+    int32_t kf_interval; /* frame k > 0 with k % kf_interval == 0 becomes a keyframe; 0 = never */
+    int32_t precision;   /* arithmetic and state precision: 32 (float) or 64 (double) */
+    int32_t reserved[7]; /* must be zero */
+} pixvod_params;
+
+typedef struct pixvod_handle pixvod_handle;
+
+/* Timing collected while profiling is enabled (pixvod_set_profiling). */
+typedef struct {
+    int64_t sweep_launches;   /* sweep-kernel launches timed */
+    double sweep_ms;          /* summed CUDA-event time of those launches */
+    int64_t kernel_launches;  /* all kernels this handle launched since enabling */
+} pixvod_profile;
+
+/* Static description of the library (no CUDA calls). */
+const char* pixvod_status_string(pixvod_status s);
+int pixvod_abi_version(void);
+pixvod_params pixvod_params_default(void);
+
+/* Bytes of device workspace a handle needs for these intrinsics and params
+ * (no CUDA calls). EINVAL for invalid intrinsics or params. */
+pixvod_status pixvod_workspace_bytes(const pixvod_intrinsics* K, const pixvod_params* p,
+                                     size_t* out_bytes);
+
+/* Bytes per pixel of the per-sweep state the sweep kernel reads and writes
+ * (one copy), for the given precision (32 or 64). No CUDA calls. */
+size_t pixvod_state_bytes_per_pixel(int32_t precision);
+
+/* Create a handle. d_workspace: caller-owned device buffer of at least
+ * pixvod_workspace_bytes, 256-byte aligned; it must outlive the handle and is not
+ * freed by pixvod_destroy. stream: a cudaStream_t (NULL = legacy default
+ * stream). Enqueues a memset of the workspace. EINVAL on null or misaligned
+ * workspace, invalid intrinsics (fx, fy <= 0, width or height < 2) or params
+ * (any sigma <= 0, damping outside [0, 1), precision not 32/64, nonzero
+ * reserved); ENOMEM if ws_bytes is too small. */
+pixvod_status pixvod_create(const pixvod_intrinsics* K, const pixvod_params* p, void* d_workspace,
+                            size_t ws_bytes, void* stream, pixvod_handle** out);
+
+/* Release the host-side handle (frees nothing the caller owns). NULL is a no-op. */
+pixvod_status pixvod_destroy(pixvod_handle* h);
+
+/* Consume one frame (Sec. 3.5, Sec. 4.3). d_frame: width*height float32 device
+ * intensities in [0, 1]. Frame 0 becomes the keyframe (no sweeps). A later
+ * frame is the target: n_iters synchronous sweeps run from the previous frame's
+ * state, then the pose average is reduced on the device. If the frame index is
+ * a multiple of kf_interval, the frame then becomes the next keyframe: the
+ * device composes T_cam<-world, resets poses and messages, and sets the log-depth
+ * and its prior mean to the segment's mean log-depth. d_normals (width*height*3
+ * float32 camera-frame unit normals of this frame, or NULL) is required exactly
+ * when the frame becomes a keyframe (EINVAL otherwise, nothing enqueued).
+ * n_iters >= 0. Asynchronous; capturable in a CUDA graph (no host sync). */
+pixvod_status pixvod_track(pixvod_handle* h, const float* d_frame, const float* d_normals,
+                           int32_t n_iters);
+
+/* As pixvod_track, with host inputs: the frame (and normals, when given) are
+ * copied into the workspace's staging buffers with cudaMemcpyAsync first. Host
+ * buffers must stay valid until the stream has passed the copies (pinned host
+ * memory makes the copies asynchronous). */
+pixvod_status pixvod_track_host(pixvod_handle* h, const float* h_frame, const float* h_normals,
+                                int32_t n_iters);
+
+/* Run n_iters more sweeps on the current target frame and reduce the pose again
+ * (no new frame, no keyframe decision). ESTATE before the first target frame. */
+pixvod_status pixvod_sweep(pixvod_handle* h, int32_t n_iters);
+
+/* xi_est of the last frame relative to the keyframe it was tracked against,
+ * [theta; rho] (App. C.2). Synchronises the stream. */
+pixvod_status pixvod_get_pose(pixvod_handle* h, double xi[6]);
+
+/* T_cam<-world of the last frame, 4x4 row-major; the world frame is the first
+ * keyframe's camera. Synchronises the stream. */
+pixvod_status pixvod_get_pose_global(pixvod_handle* h, double T[16]);
+
+/* Asynchronous copy of xi_est (6 doubles) to device memory. */
+pixvod_status pixvod_get_pose_device(pixvod_handle* h, double* d_xi);
+
+/* Depth exp(mu_6) (resp. inverse depth exp(-mu_6)) of every keyframe pixel,
+ * width*height float32 into caller device memory. Asynchronous. */
+pixvod_status pixvod_get_depth(pixvod_handle* h, float* d_depth);
+pixvod_status pixvod_get_inv_depth(pixvod_handle* h, float* d_inv_depth);
+
+/* Sticky device flags (PIXVOD_FLAG_*). Synchronises the stream. Returns
+ * ENUMERIC when any flag is set, OK otherwise. */
+pixvod_status pixvod_get_status(pixvod_handle* h, uint32_t* flags);
+
+/* Checkpoint of the full sweep state: a 256-byte header, the state planes, the
+ * input planes and the device scalars. Header (little-endian int64 words):
+ *   [0] magic 0x50495856  [1] version 1  [2] precision (32/64)  [3] width
+ *   [4] height  [5] pitch (elements per plane row)  [6] state planes (151)
+ *   [7] frame index  [8] byte offset of the planes  [9] byte offset of the scalars
+ *   [10] input planes (6)  [11] 1 if a target frame is loaded
+ * Each plane is height*pitch elements of the state precision. State planes:
+ *   0..6     mu: xi_0..xi_5 (theta, rho), log-depth
+ *   7..27    M_p: pose information of the belief without the photometric factor
+ *            (pose prior plus identity messages), 6x6 lower triangle packed row
+ *            by row ((0,0),(1,0),(1,1),(2,0),...)
+ *   28..33   u: the depth-marginalised pose information of the belief is
+ *            P = M_p + u u^T
+ *   34       s: pose-marginalised log-depth information of the belief
+ *   35+27k.. identity-factor message into the pixel from slot k (k = 0 left,
+ *            1 right, 2 up, 3 down): 21 packed Lambda then 6 eta
+ *   143+2k.. normal-integration message from slot k: Lambda, eta
+ * Input planes: keyframe intensity I_s, target intensity I_t, its gradients
+ * g_x, g_y, normal-integration edge measurements m_x (to the right neighbour),
+ * m_y (to the lower neighbour).
+ * Scalars (doubles): xi_est[6], T_kf[16] (T_kf<-world), T_cur[16], d_prior,
+ * d_mean.
+ * pixvod_state_size returns the byte count. save synchronises the stream; load
+ * enqueues the copies (the host buffer must outlive them) and restores the
+ * frame index. EINVAL on a size, magic or geometry mismatch. */
+pixvod_status pixvod_state_size(pixvod_handle* h, size_t* bytes);
+pixvod_status pixvod_save_state(pixvod_handle* h, void* h_buf, size_t bytes);
+pixvod_status pixvod_load_state(pixvod_handle* h, const void* h_buf, size_t bytes);
+
+/* Per-kernel timing: when enabled, CUDA events are recorded around every sweep
+ * launch on the handle's stream; pixvod_get_profile synchronises and returns
+ * the totals since enabling. */
+pixvod_status pixvod_set_profiling(pixvod_handle* h, int32_t enable);
+pixvod_status pixvod_get_profile(pixvod_handle* h, pixvod_profile* out);
+
+/* Number of kernels this handle has launched since creation. */
+pixvod_status pixvod_launch_count(pixvod_handle* h, int64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIXVOD_H */

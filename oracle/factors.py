@@ -9,8 +9,11 @@ Lambda_f = J^T Lambda J, eta_f = -J^T Lambda r_bar.
 
 Readings of points the paper leaves open (each also listed in the design notes):
 * pixel centres are at integer coordinates; a warped point is valid iff Z > 1e-6
-  and 0 <= x <= W-1, 0 <= y <= H-1 (inclusive); an invalid pixel contributes no
-  photometric factor (the overlap domain Omega(mu) of Eq. 1);
+  and -1e-3 <= x <= W-1+1e-3, -1e-3 <= y <= H-1+1e-3 (the margin keeps pixels that
+  the identity pose maps exactly onto the border valid whatever the rounding; the
+  sample point is clamped into the image); an invalid pixel contributes no
+  photometric factor (the overlap domain Omega(mu) of Eq. 1), and neither does a
+  pixel whose residual or interpolated gradient is not finite (NaN input);
 * image gradients are central differences with replicated borders, bilinearly
   interpolated at the warped point like the intensity;
 * the Huber threshold t acts on the Mahalanobis residual |r|/sigma_D and the robust
@@ -70,8 +73,14 @@ def warp(xi, d, u, v, K: Intrinsics):
     return x, y, Z, X_s, X_t, R
 
 
+BORDER_MARGIN = 1e-3
+
+
 def warp_valid(x, y, Z, K: Intrinsics):
-    return (Z > Z_MIN) & (x >= 0) & (x <= K.width - 1) & (y >= 0) & (y <= K.height - 1)
+    """Overlap domain: positive depth and inside the image, with a 1e-3 px margin
+    (a pixel warped by the identity pose lands exactly on the border)."""
+    m = BORDER_MARGIN
+    return (Z > Z_MIN) & (x >= -m) & (x <= K.width - 1 + m) & (y >= -m) & (y <= K.height - 1 + m)
 
 
 # --------------------------------------------------------------------------
@@ -142,6 +151,9 @@ def photometric_factor(xi, d, u, v, I_s_p, I_t, g_x, g_y, K: Intrinsics, sigma_D
     Returns Lambda (..., 7, 7), eta (..., 7), and diagnostics (r, J, w, valid)."""
     r, valid = photometric_residual(xi, d, u, v, I_s_p, I_t, K)
     J = photometric_jacobian(xi, d, u, v, g_x, g_y, K)
+    valid = valid & np.isfinite(r) & np.all(np.isfinite(J), axis=-1)
+    J = np.where(valid[..., None], J, 0.0)
+    r = np.where(valid, r, 0.0)
     w = huber_weight(r / sigma_D, t_huber)
     lam = np.where(valid, w / sigma_D ** 2, 0.0)
     r = np.where(valid, r, 0.0)

@@ -1,0 +1,538 @@
+// PixVOD sweep kernels (templated on the arithmetic type).
+//
+// State: structure-of-arrays planes of height x pitch elements, ping-ponged
+// between two buffers (a sweep reads one, writes every plane of the other).
+//   0..6     mu (xi_0..xi_5, log-depth d)
+//   7..27    M_p: pose information of the belief without the photometric factor
+//            (pose prior plus the four identity messages), 6x6 packed lower
+//   28..33   u: photometric part of the depth-marginalised pose information,
+//            P = M_p + u u^T
+//   34       s: belief information of the depth with the pose marginalised
+//   35+27k   identity-factor message into the pixel from slot k: Lambda (21
+//            packed lower) then eta (6); slots 0 left, 1 right, 2 up, 3 down
+//   143+2k   normal-integration message from slot k: Lambda, eta
+//
+// After every sweep the stored beliefs are projected to the new linearisation
+// point, where their eta is zero; the variable-to-factor message of pixel j
+// towards a pairwise factor f is then belief minus that factor's message, and
+// its marginal on the factor's dims is (P_j - Lambda_{f->j}, -eta_{f->j}) for an
+// identity factor and (s_j - n_{f->j}, -e_{f->j}) for a normal factor, because
+// each of those messages lives on one block (pose or depth) only. P_j is kept
+// as M_p + u u^T because a single pixel's rank-one photometric information can
+// exceed its other pose information by more than float32 resolves.
+#pragma once
+
+#include "pv_math.cuh"
+
+namespace pv {
+
+constexpr int N_PLANES = 151;
+constexpr int PL_MU = 0;
+constexpr int PL_MP = 7;
+constexpr int PL_U = 28;
+constexpr int PL_S = 34;
+constexpr int PL_ID = 35;
+constexpr int ID_STRIDE = 27;
+constexpr int PL_NM = 143;
+constexpr int N_INPUT_PLANES = 6;  // I_s, I_t, g_x, g_y, m_x, m_y
+
+constexpr unsigned FLAG_NONPOS_PIVOT = 0x1u;
+constexpr unsigned FLAG_NONFINITE = 0x2u;
+
+// Device-resident per-handle scalars (doubles, fixed layout; the checkpoint
+// format copies the first 40).
+struct Scalars {
+    double xi_est[6];
+    double T_kf[16];   // T_kf<-world
+    double T_cur[16];  // T_cam<-world of the last frame
+    double d_prior;    // log-depth prior mean of the current keyframe segment
+    double d_mean;     // mean log-depth after the last reduction
+    unsigned flags;
+    unsigned counter;  // last-block ticket of the reduction
+    double pad[6];
+};
+
+template <typename T>
+struct Geometry {
+    int W, H, pitch;
+    size_t plane;  // elements per plane
+    T fx, fy, cx, cy, ifx, ify;
+};
+
+template <typename T>
+struct Factors {
+    T lam_D, inv_sigma_D, t_huber, lam_P, lam_R, lam_N, lam_Z, beta;
+};
+
+template <typename T>
+struct SweepArgs {
+    Geometry<T> g;
+    Factors<T> f;
+    const T* __restrict__ in;
+    T* __restrict__ out;
+    const T* __restrict__ I_s;
+    const T* __restrict__ I_t;
+    const T* __restrict__ g_x;
+    const T* __restrict__ g_y;
+    const T* __restrict__ m_x;
+    const T* __restrict__ m_y;
+    Scalars* sc;
+};
+
+// ---------------------------------------------------------------------------
+// a0: frame ingest
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void normal_slopes(const float* __restrict__ n, int u, int v, const Geometry<T>& g,
+                                              T* ax, T* ay) {
+    T nx = T(n[0]), ny = T(n[1]), nz = T(n[2]);
+    T nr = nx * (T(u) - g.cx) / g.fx + ny * (T(v) - g.cy) / g.fy + nz;
+    bool ok = v_abs(nr) >= T(1e-3);
+    *ax = ok ? nx / (g.fx * nr) : T(0);
+    *ay = ok ? ny / (g.fy * nr) : T(0);
+}
+
+// Keyframe: source intensities and the normal-integration edge measurements of
+// Eq. 6 (m_x between (u, v) and (u+1, v), m_y between (u, v) and (u, v+1)).
+template <typename T>
+__global__ void k_ingest_keyframe(Geometry<T> g, const float* __restrict__ frame,
+                                  const float* __restrict__ normals, T* I_s, T* m_x, T* m_y) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = blockIdx.y * blockDim.y + threadIdx.y;
+    if (u >= g.W || v >= g.H) return;
+    size_t i = (size_t)v * g.pitch + u;
+    size_t f = (size_t)v * g.W + u;
+    I_s[i] = T(frame[f]);
+    T ax, ay;
+    normal_slopes(normals + 3 * f, u, v, g, &ax, &ay);
+    T mx = T(0), my = T(0);
+    if (u + 1 < g.W) {
+        T bx, by;
+        normal_slopes(normals + 3 * (f + 1), u + 1, v, g, &bx, &by);
+        mx = T(0.5) * (ax + bx);
+    }
+    if (v + 1 < g.H) {
+        T bx, by;
+        normal_slopes(normals + 3 * (f + g.W), u, v + 1, g, &bx, &by);
+        my = T(0.5) * (ay + by);
+    }
+    m_x[i] = mx;
+    m_y[i] = my;
+}
+
+// Target: intensities and central-difference gradients (replicated borders).
+template <typename T>
+__global__ void k_ingest_target(Geometry<T> g, const float* __restrict__ frame, T* I_t, T* g_x, T* g_y) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = blockIdx.y * blockDim.y + threadIdx.y;
+    if (u >= g.W || v >= g.H) return;
+    size_t i = (size_t)v * g.pitch + u;
+    const float* row = frame + (size_t)v * g.W;
+    int ul = u > 0 ? u - 1 : 0, ur = u + 1 < g.W ? u + 1 : g.W - 1;
+    int vu = v > 0 ? v - 1 : 0, vd = v + 1 < g.H ? v + 1 : g.H - 1;
+    I_t[i] = T(row[u]);
+    g_x[i] = T(0.5) * (T(row[ur]) - T(row[ul]));
+    g_y[i] = T(0.5) * (T(frame[(size_t)vd * g.W + u]) - T(frame[(size_t)vu * g.W + u]));
+}
+
+// Keyframe reset: identity pose, log-depth at the segment's prior mean, no
+// messages, belief equal to the priors (M_p = lam_P I, u = 0, s = lam_Z).
+template <typename T>
+__global__ void k_reset(Geometry<T> g, Factors<T> f, T* state, const Scalars* sc) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = blockIdx.y * blockDim.y + threadIdx.y;
+    if (u >= g.W || v >= g.H) return;
+    size_t i = (size_t)v * g.pitch + u;
+    T d0 = T(sc->d_prior);
+    for (int p = 0; p < N_PLANES; ++p) state[(size_t)p * g.plane + i] = T(0);
+    state[(size_t)6 * g.plane + i] = d0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) state[(size_t)(PL_MP + pidx(k, k)) * g.plane + i] = f.lam_P;
+    state[(size_t)PL_S * g.plane + i] = f.lam_Z;
+}
+
+// ---------------------------------------------------------------------------
+// a1-a4: one synchronous sweep (v1: one thread per pixel, global loads)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T bilinear(const T* __restrict__ img, int pitch, int x0, int y0, int x1, int y1,
+                                      T ax, T ay) {
+    T a = img[(size_t)y0 * pitch + x0], b = img[(size_t)y0 * pitch + x1];
+    T c = img[(size_t)y1 * pitch + x0], d = img[(size_t)y1 * pitch + x1];
+    return (T(1) - ay) * ((T(1) - ax) * a + ax * b) + ay * ((T(1) - ax) * c + ax * d);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_sweep(const SweepArgs<T> a) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.y * blockDim.y + threadIdx.y;
+    const Geometry<T>& g = a.g;
+    const Factors<T>& F = a.f;
+    if (u >= g.W || v >= g.H) return;
+    const size_t PS = g.plane;
+    const size_t i = (size_t)v * g.pitch + u;
+    const T* __restrict__ S = a.in;
+    T* __restrict__ D = a.out;
+
+    T xi[6], d;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) xi[k] = S[k * PS + i];
+    d = S[6 * PS + i];
+    T R[9], t[3];
+    se3_exp(xi, R, t);
+
+    // The belief has the exact structure
+    //   Lambda_b = blockdiag(M_p, m_d) + alpha J J^T,  eta_b = eta_o - alpha r J
+    // (identity messages and the pose prior act on the pose block, normal messages
+    // and the depth prior on the depth, the photometric factor is rank one), so it
+    // is kept in that form: M_p (packed), m_d, alpha, J, r and eta_o (in eb).
+    T eb[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) eb[q] = T(0);
+    T alpha = T(0), rph = T(0);
+    T J[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) J[q] = T(0);
+
+    // --- a1: photometric factor (Eqs. 2, 3) at the current mean ---
+    {
+        T z = v_exp(d);
+        T Xs[3] = {z * (T(u) - g.cx) * g.ifx, z * (T(v) - g.cy) * g.ify, z};
+        T Xt[3];
+        mat3_vec(R, Xs, Xt);
+        Xt[0] += t[0];
+        Xt[1] += t[1];
+        Xt[2] += t[2];
+        T Z = Xt[2];
+        bool valid = Z > T(1e-6);
+        T iz = valid ? T(1) / Z : T(0);
+        T x = g.fx * Xt[0] * iz + g.cx;
+        T y = g.fy * Xt[1] * iz + g.cy;
+        // overlap test with a 1e-3 px margin (pixels warped by the identity land on
+        // the border exactly); the sample point is clamped into the image
+        valid = valid && (x >= T(-1e-3)) && (x <= T(g.W - 1) + T(1e-3)) && (y >= T(-1e-3)) &&
+                (y <= T(g.H - 1) + T(1e-3));
+        T r = T(0), gx = T(0), gy = T(0);
+        if (valid) {
+            x = x < T(0) ? T(0) : (x > T(g.W - 1) ? T(g.W - 1) : x);
+            y = y < T(0) ? T(0) : (y > T(g.H - 1) ? T(g.H - 1) : y);
+            int x0 = (int)v_floor(x), y0 = (int)v_floor(y);
+            x0 = min(x0, g.W - 1);
+            y0 = min(y0, g.H - 1);
+            int x1 = min(x0 + 1, g.W - 1), y1 = min(y0 + 1, g.H - 1);
+            T ax = x - T(x0), ay = y - T(y0);
+            T It = bilinear(a.I_t, g.pitch, x0, y0, x1, y1, ax, ay);
+            gx = bilinear(a.g_x, g.pitch, x0, y0, x1, y1, ax, ay);
+            gy = bilinear(a.g_y, g.pitch, x0, y0, x1, y1, ax, ay);
+            r = a.I_s[i] - It;
+            valid = v_finite(r) && v_finite(gx) && v_finite(gy);
+        }
+        if (valid) {
+            // dr/dX_t = -(gx, gy) d(pi)/dX_t
+            T a0 = -gx * g.fx * iz, a1 = -gy * g.fy * iz;
+            T a2 = (gx * g.fx * Xt[0] + gy * g.fy * Xt[1]) * iz * iz;
+            T av[3] = {a0, a1, a2}, b[3];
+            mat3T_vec(R, av, b);  // b = R^T a
+            J[0] = Xs[1] * b[2] - Xs[2] * b[1];
+            J[1] = Xs[2] * b[0] - Xs[0] * b[2];
+            J[2] = Xs[0] * b[1] - Xs[1] * b[0];
+            J[3] = b[0];
+            J[4] = b[1];
+            J[5] = b[2];
+            J[6] = b[0] * Xs[0] + b[1] * Xs[1] + b[2] * Xs[2];
+            T M = v_abs(r) * F.inv_sigma_D;
+            T w = M > F.t_huber ? (T(2) * F.t_huber * M - F.t_huber * F.t_huber) / (M * M) : T(1);
+            alpha = w * F.lam_D;
+            rph = r;
+        }
+    }
+    // --- priors (Eq. 4 with identity Jacobian; log-depth prior) ---
+    T Mp[21];
+#pragma unroll
+    for (int q = 0; q < 21; ++q) Mp[q] = T(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        Mp[pidx(k, k)] = F.lam_P;
+        eb[k] -= F.lam_P * xi[k];
+    }
+    T md = F.lam_Z;
+    eb[6] -= F.lam_Z * (d - T(a.sc->d_prior));
+
+    // --- a2/a3: pairwise messages from the four neighbours ---
+    T Mk[4][27];
+    T Nk[4][2];
+    unsigned flags = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int un = u + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+        const int vn = v + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+        const bool has = un >= 0 && un < g.W && vn >= 0 && vn < g.H;
+        if (!has) {
+#pragma unroll
+            for (int q = 0; q < 27; ++q) Mk[k][q] = T(0);
+            Nk[k][0] = T(0);
+            Nk[k][1] = T(0);
+            continue;
+        }
+        const size_t j = (size_t)vn * g.pitch + un;
+        const int ko = k ^ 1;
+        // identity factor (Eq. 5): r = Log(Exp(xi_j)^-1 Exp(xi_i)), J_i = I, J_j = -I
+        T xj[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) xj[q] = S[q * PS + j];
+        T Rj[9], tj[3], Rr[9], tr[3], rb[6];
+        se3_exp(xj, Rj, tj);
+        se3_invmul(Rj, tj, R, t, Rr, tr);
+        se3_log(Rr, tr, rb);
+        // variable-to-factor marginal of j: V = W + u u^T with W = M_p,j - Lambda_{f->j}
+        // (pose prior plus j's three other identity messages) and u = u_j
+        T W[21], C[21], ev[6], uj[6];
+#pragma unroll
+        for (int q = 0; q < 21; ++q) {
+            W[q] = S[(PL_MP + q) * PS + j] - S[(PL_ID + ID_STRIDE * ko + q) * PS + j];
+            C[q] = W[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            ev[q] = -S[(PL_ID + ID_STRIDE * ko + 21 + q) * PS + j];
+            uj[q] = S[(PL_U + q) * PS + j];
+        }
+        // A = W + lam_R I is well conditioned (W is bounded by a few lam_R)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) C[pidx(q, q)] += F.lam_R;
+        T idg[6];
+        if (!chol_packed<6>(C, idg)) flags |= FLAG_NONPOS_PIVOT;
+        // Lambda_msg = lam_R C^-1 V with C = A + u u^T:
+        //   = W - (L^-1 W)^T (L^-1 W) + lam_R^2 / (1 + u^T z) z z^T,  z = A^-1 u
+        T Y[6][6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+#pragma unroll
+            for (int r = 0; r < 6; ++r) Y[c][r] = W[pidx(r, c)];
+            fwd_solve<6>(C, idg, Y[c]);
+        }
+        T z[6], gv[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            z[q] = uj[q];
+            T wr = T(0);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) wr += W[pidx(q, c)] * rb[c];
+            gv[q] = ev[q] - wr;  // g0 = eta_v - W r
+        }
+        fwd_solve<6>(C, idg, z);
+        bwd_solve<6>(C, idg, z);
+        fwd_solve<6>(C, idg, gv);
+        bwd_solve<6>(C, idg, gv);  // h = A^-1 g0
+        T uz = T(0), ur = T(0), uh = T(0);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            uz += uj[q] * z[q];
+            ur += uj[q] * rb[q];
+            uh += uj[q] * gv[q];
+        }
+        const T iuz = T(1) / (T(1) + uz);
+        const T crank = F.lam_R * F.lam_R * iuz;
+        // eta_msg = lam_R C^-1 (eta_v - V r) = lam_R (h - z (u^T r + u^T h) / (1 + u^T z))
+        const T ecoef = (ur + uh) * iuz;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) gv[q] -= ecoef * z[q];
+        const T beta = F.beta, omb = T(1) - F.beta;
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int c = 0; c <= r; ++c) {
+                T yy = T(0);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) yy += Y[r][q] * Y[c][q];
+                T lnew = W[pidx(r, c)] - yy + crank * z[r] * z[c];
+                T lold = S[(PL_ID + ID_STRIDE * k + pidx(r, c)) * PS + i];
+                Mk[k][pidx(r, c)] = omb * lnew + beta * lold;
+            }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            T eold = S[(PL_ID + ID_STRIDE * k + 21 + q) * PS + i];
+            Mk[k][21 + q] = omb * (F.lam_R * gv[q]) + beta * eold;
+        }
+#pragma unroll
+        for (int q = 0; q < 21; ++q) Mp[q] += Mk[k][q];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) eb[q] += Mk[k][21 + q];
+
+        // normal-integration factor (Eq. 6): r_i = d_i - d_j + sg m
+        T dj = S[6 * PS + j];
+        T sv = S[PL_S * PS + j] - S[(PL_NM + 2 * ko) * PS + j];
+        T evn = -S[(PL_NM + 2 * ko + 1) * PS + j];
+        T m = k == 0 ? a.m_x[i - 1] : (k == 1 ? a.m_x[i] : (k == 2 ? a.m_y[i - g.pitch] : a.m_y[i]));
+        T sg = (k == 0 || k == 2) ? T(1) : T(-1);
+        T rn = d - dj + sg * m;
+        T den = T(1) / (F.lam_N + sv);
+        T nnew = F.lam_N * sv * den;
+        T enew = F.lam_N * (evn - sv * rn) * den;
+        Nk[k][0] = omb * nnew + beta * S[(PL_NM + 2 * k) * PS + i];
+        Nk[k][1] = omb * enew + beta * S[(PL_NM + 2 * k + 1) * PS + i];
+        md += Nk[k][0];
+        eb[6] += Nk[k][1];
+    }
+
+    // --- a4: belief, mean update, tangent projection ---
+    // With B = blockdiag(M_p, m_d), h = B^-1 eta_o and z = B^-1 J, Sherman-Morrison
+    // gives tau = Lambda_b^-1 eta_b = h - z alpha (r + J^T h) / (1 + alpha J^T z),
+    // and the marginals of Lambda_b are, with q = J_p^T M_p^-1 J_p,
+    //   P = M_p + u u^T,  u = sqrt(alpha m_d / (m_d + alpha J_d^2)) J_p,
+    //   s = m_d + alpha J_d^2 / (1 + alpha q),
+    // all free of cancellation.
+    T Lp[21], idp[6];
+#pragma unroll
+    for (int q = 0; q < 21; ++q) Lp[q] = Mp[q];
+    bool ok = chol_packed<6>(Lp, idp);
+    T up[6], gp[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        up[q] = J[q];
+        gp[q] = eb[q];
+    }
+    fwd_solve<6>(Lp, idp, up);
+    bwd_solve<6>(Lp, idp, up);
+    fwd_solve<6>(Lp, idp, gp);
+    bwd_solve<6>(Lp, idp, gp);
+    T qv = T(0), jh = T(0);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        qv += J[q] * up[q];
+        jh += J[q] * gp[q];
+    }
+    const T imd = T(1) / md;
+    const T hd = eb[6] * imd;
+    const T zd = J[6] * imd;
+    const T coef = alpha * (rph + jh + J[6] * hd) / (T(1) + alpha * (qv + J[6] * zd));
+    T tau[7];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) tau[q] = gp[q] - coef * up[q];
+    tau[6] = hd - coef * zd;
+    bool fin = true;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) fin = fin && v_finite(tau[q]);
+    if (!ok) flags |= FLAG_NONPOS_PIVOT;
+    if (!ok || !fin) {
+        if (!fin) flags |= FLAG_NONFINITE;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) tau[q] = T(0);
+    }
+    // mu <- mu (+) tau
+    {
+        T Rt[9], tt[3], Rn[9], tn[3], xn[6];
+        se3_exp(tau, Rt, tt);
+        se3_mul(R, t, Rt, tt, Rn, tn);
+        se3_log(Rn, tn, xn);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) D[q * PS + i] = xn[q];
+        D[6 * PS + i] = d + tau[6];
+    }
+    {
+        const T bp = alpha * md / (md + alpha * J[6] * J[6]);
+        const T sb = v_sqrt(bp);
+#pragma unroll
+        for (int q = 0; q < 21; ++q) D[(PL_MP + q) * PS + i] = Mp[q];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) D[(PL_U + q) * PS + i] = sb * J[q];
+        D[PL_S * PS + i] = md + alpha * J[6] * J[6] / (T(1) + alpha * qv);
+    }
+    // messages, projected: eta <- eta - Lambda tau
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int q = 0; q < 21; ++q) D[(PL_ID + ID_STRIDE * k + q) * PS + i] = Mk[k][q];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            T s = Mk[k][21 + r];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) s -= Mk[k][pidx(r, c)] * tau[c];
+            D[(PL_ID + ID_STRIDE * k + 21 + r) * PS + i] = s;
+        }
+        D[(PL_NM + 2 * k) * PS + i] = Nk[k][0];
+        D[(PL_NM + 2 * k + 1) * PS + i] = Nk[k][1] - Nk[k][0] * tau[6];
+    }
+    if (flags) atomicOr(&a.sc->flags, flags);
+}
+
+// ---------------------------------------------------------------------------
+// a5: pose average (App. C.2) and keyframe anchoring, one launch, fixed order
+// ---------------------------------------------------------------------------
+constexpr int RED_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce(Geometry<T> g, const T* __restrict__ state,
+                                                        double* __restrict__ partials, Scalars* sc,
+                                                        int anchor) {
+    __shared__ double sh[7][RED_THREADS];
+    __shared__ bool last;
+    const int tid = threadIdx.x;
+    const size_t n = (size_t)g.W * g.H;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (size_t p = (size_t)blockIdx.x * RED_THREADS + tid; p < n; p += (size_t)gridDim.x * RED_THREADS) {
+        size_t v = p / g.W, u = p - v * g.W;
+        size_t i = v * g.pitch + u;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) acc[q] += double(state[q * g.plane + i]);
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) sh[q][tid] = acc[q];
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (tid < s)
+#pragma unroll
+            for (int q = 0; q < 7; ++q) sh[q][tid] += sh[q][tid + s];
+        __syncthreads();
+    }
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) partials[blockIdx.x * 7 + q] = sh[q][0];
+        __threadfence();
+        unsigned ticket = atomicAdd(&sc->counter, 1u);
+        last = ticket == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last block sums the partials in block order
+    if (tid < 7) {
+        double s = 0;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(partials + b * 7 + tid);
+        sh[tid][0] = s / double(n);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double xi[6], R[9], t[3];
+        for (int q = 0; q < 6; ++q) {
+            xi[q] = sh[q][0];
+            sc->xi_est[q] = xi[q];
+        }
+        sc->d_mean = sh[6][0];
+        se3_exp(xi, R, t);
+        // T_cur = Exp(xi_est) T_kf with Exp(xi_est) = [R t; 0 1]
+        double Tc[16];
+        for (int c = 0; c < 4; ++c) {
+            for (int r = 0; r < 3; ++r)
+                Tc[4 * r + c] = R[3 * r] * sc->T_kf[c] + R[3 * r + 1] * sc->T_kf[4 + c] +
+                                R[3 * r + 2] * sc->T_kf[8 + c] + t[r] * sc->T_kf[12 + c];
+            Tc[12 + c] = sc->T_kf[12 + c];
+        }
+        for (int q = 0; q < 16; ++q) sc->T_cur[q] = Tc[q];
+        if (anchor) {
+            for (int q = 0; q < 16; ++q) sc->T_kf[q] = Tc[q];
+            sc->d_prior = sc->d_mean;
+        }
+        sc->counter = 0;
+    }
+}
+
+// Depth output: exp(sign * mu_6) as dense float32.
+template <typename T>
+__global__ void k_depth_out(Geometry<T> g, const T* __restrict__ state, float* out, T sign) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = blockIdx.y * blockDim.y + threadIdx.y;
+    if (u >= g.W || v >= g.H) return;
+    out[(size_t)v * g.W + u] = float(v_exp(sign * state[6 * g.plane + (size_t)v * g.pitch + u]));
+}
+
+}  // namespace pv

@@ -1,0 +1,250 @@
+// Device math for the PixVOD sweep kernels: SE(3) exponential / logarithm,
+// packed symmetric storage, Cholesky factorisation and triangular solves.
+// Templated on the arithmetic type (float for the production path, double for
+// the verification path).
+//
+// se(3) convention (App. C.2): xi = [theta; rho], Exp(xi) = (Exp_SO3(theta),
+// V(theta) rho), V = I + B [theta]x + C [theta]x^2, A = sin t / t,
+// B = (1 - cos t)/t^2, C = (t - sin t)/t^3 with t = |theta|.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace pv {
+
+// ---------------------------------------------------------------------------
+// scalar wrappers (precise CUDA math functions, selected by type)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float v_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double v_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float v_exp(float x) { return expf(x); }
+__device__ __forceinline__ double v_exp(double x) { return exp(x); }
+__device__ __forceinline__ float v_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double v_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float v_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double v_floor(double x) { return floor(x); }
+__device__ __forceinline__ float v_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double v_abs(double x) { return fabs(x); }
+__device__ __forceinline__ void v_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void v_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ bool v_finite(float x) { return isfinite(x); }
+__device__ __forceinline__ bool v_finite(double x) { return isfinite(x); }
+
+// Precision-dependent series limits: below `tiny` the A/B quotients use two
+// Taylor terms; below 1 rad the C and D coefficients use their power series
+// with enough terms for the type's epsilon.
+template <typename T> struct Prec;
+template <> struct Prec<float> {
+    static constexpr float tiny = 1e-4f;
+    static constexpr int c_terms = 7;
+    static constexpr float d_series_max = 1.0f;
+};
+template <> struct Prec<double> {
+    static constexpr double tiny = 1e-8;
+    static constexpr int c_terms = 12;
+    static constexpr double d_series_max = 0.5;
+};
+
+// (t - sin t)/t^3 = sum_k (-1)^k t^(2k) / (2k+3)!
+template <typename T>
+__device__ __forceinline__ T series_C(T t2) {
+    T term = T(1) / T(6);
+    T sum = term;
+#pragma unroll
+    for (int k = 1; k < Prec<T>::c_terms; ++k) {
+        term = -term * t2 / T((2 * k + 2) * (2 * k + 3));
+        sum += term;
+    }
+    return sum;
+}
+
+// D(t) = (1 - A/(2B))/t^2 = 1/t^2 - cot(t/2)/(2t), the [theta]x^2 coefficient of
+// V^-1; from the Laurent series of cot: 1/12 + t^2/720 + t^4/30240 + t^6/1209600
+// + t^8/47900160 + t^10/1892437580.3 + ... (used below d_series_max).
+template <typename T>
+__device__ __forceinline__ T series_D(T t2) {
+    return T(1) / T(12) + t2 * (T(1) / T(720) + t2 * (T(1) / T(30240) + t2 * (T(1) / T(1209600) +
+           t2 * (T(1) / T(47900160) + t2 * (T(1) / T(1892437580.3183))))));
+}
+
+template <typename T>
+__device__ __forceinline__ void coef_AB(T t, T* A, T* B) {
+    if (t < Prec<T>::tiny) {
+        T t2 = t * t;
+        *A = T(1) - t2 / T(6);
+        *B = T(0.5) - t2 / T(24);
+    } else {
+        T s, c, sh, ch;
+        v_sincos(t, &s, &c);
+        v_sincos(T(0.5) * t, &sh, &ch);
+        *A = s / t;
+        T q = sh / (T(0.5) * t);
+        *B = T(0.5) * q * q;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T coef_C(T t, T A) {
+    if (t < T(1)) return series_C(t * t);
+    return (T(1) - A) / (t * t);
+}
+
+template <typename T>
+__device__ __forceinline__ T coef_D(T t, T A, T B) {
+    if (t < Prec<T>::d_series_max) return series_D(t * t);
+    return (T(1) - A / (T(2) * B)) / (t * t);
+}
+
+// ---------------------------------------------------------------------------
+// 3x3 helpers (row-major)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void mat3_mul(const T* a, const T* b, T* c) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            c[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+}
+
+template <typename T>
+__device__ __forceinline__ void mat3_vec(const T* a, const T* x, T* y) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[i] = a[3 * i] * x[0] + a[3 * i + 1] * x[1] + a[3 * i + 2] * x[2];
+}
+
+template <typename T>
+__device__ __forceinline__ void mat3T_vec(const T* a, const T* x, T* y) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[i] = a[i] * x[0] + a[3 + i] * x[1] + a[6 + i] * x[2];
+}
+
+// M = I + a W + b W^2 for W = [w]x, using W^2 = w w^T - |w|^2 I
+template <typename T>
+__device__ __forceinline__ void so3_poly(const T* w, T a, T b, T* M) {
+    T t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    M[0] = T(1) + b * (w[0] * w[0] - t2);
+    M[4] = T(1) + b * (w[1] * w[1] - t2);
+    M[8] = T(1) + b * (w[2] * w[2] - t2);
+    M[1] = -a * w[2] + b * w[0] * w[1];
+    M[3] = a * w[2] + b * w[0] * w[1];
+    M[2] = a * w[1] + b * w[0] * w[2];
+    M[6] = -a * w[1] + b * w[0] * w[2];
+    M[5] = -a * w[0] + b * w[1] * w[2];
+    M[7] = a * w[0] + b * w[1] * w[2];
+}
+
+// Exp: xi (6) -> R (9), t (3)
+template <typename T>
+__device__ __forceinline__ void se3_exp(const T* xi, T* R, T* t) {
+    T th = v_sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+    T A, B;
+    coef_AB(th, &A, &B);
+    T C = coef_C(th, A);
+    so3_poly(xi, A, B, R);
+    T V[9];
+    so3_poly(xi, B, C, V);
+    mat3_vec(V, xi + 3, t);
+}
+
+// Log: R (9), t (3) -> xi (6); rotation angles below pi
+template <typename T>
+__device__ __forceinline__ void se3_log(const T* R, const T* t, T* xi) {
+    T w0 = T(0.5) * (R[7] - R[5]);
+    T w1 = T(0.5) * (R[2] - R[6]);
+    T w2 = T(0.5) * (R[3] - R[1]);
+    T s = v_sqrt(w0 * w0 + w1 * w1 + w2 * w2);
+    T c = T(0.5) * (R[0] + R[4] + R[8] - T(1));
+    T th = v_atan2(s, c);
+    T A, B;
+    coef_AB(th, &A, &B);
+    T inv = T(1) / A;
+    xi[0] = w0 * inv;
+    xi[1] = w1 * inv;
+    xi[2] = w2 * inv;
+    T D = coef_D(th, A, B);
+    T Vi[9];
+    so3_poly(xi, T(-0.5), D, Vi);
+    mat3_vec(Vi, t, xi + 3);
+}
+
+// (R1, t1) * (R2, t2)
+template <typename T>
+__device__ __forceinline__ void se3_mul(const T* R1, const T* t1, const T* R2, const T* t2, T* R, T* t) {
+    mat3_mul(R1, R2, R);
+    mat3_vec(R1, t2, t);
+    t[0] += t1[0];
+    t[1] += t1[1];
+    t[2] += t1[2];
+}
+
+// (R1, t1)^-1 * (R2, t2) = (R1^T R2, R1^T (t2 - t1))
+template <typename T>
+__device__ __forceinline__ void se3_invmul(const T* R1, const T* t1, const T* R2, const T* t2, T* R, T* t) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            R[3 * i + j] = R1[i] * R2[j] + R1[3 + i] * R2[3 + j] + R1[6 + i] * R2[6 + j];
+    T d[3] = {t2[0] - t1[0], t2[1] - t1[1], t2[2] - t1[2]};
+    mat3T_vec(R1, d, t);
+}
+
+// ---------------------------------------------------------------------------
+// packed lower-triangular symmetric storage: (r, c), r >= c -> r(r+1)/2 + c
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int pidx(int r, int c) { return r >= c ? r * (r + 1) / 2 + c : c * (c + 1) / 2 + r; }
+
+// In-place Cholesky of a packed N x N SPD matrix: A = L L^T, L packed lower.
+// inv_diag receives 1 / L(j, j). Returns false on a non-positive (or NaN) pivot.
+template <int N, typename T>
+__device__ __forceinline__ bool chol_packed(T* A, T* inv_diag) {
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        T d = A[pidx(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= A[pidx(j, k)] * A[pidx(j, k)];
+        ok = ok && (d > T(0));
+        T ljj = v_sqrt(d > T(0) ? d : T(1));
+        T inv = T(1) / ljj;
+        A[pidx(j, j)] = ljj;
+        inv_diag[j] = inv;
+#pragma unroll
+        for (int i = j + 1; i < N; ++i) {
+            T v = A[pidx(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v -= A[pidx(i, k)] * A[pidx(j, k)];
+            A[pidx(i, j)] = v * inv;
+        }
+    }
+    return ok;
+}
+
+// Solve L y = b in place (L packed lower from chol_packed).
+template <int N, typename T>
+__device__ __forceinline__ void fwd_solve(const T* L, const T* inv_diag, T* b) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        T v = b[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) v -= L[pidx(i, k)] * b[k];
+        b[i] = v * inv_diag[i];
+    }
+}
+
+// Solve L^T x = y in place.
+template <int N, typename T>
+__device__ __forceinline__ void bwd_solve(const T* L, const T* inv_diag, T* b) {
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        T v = b[i];
+#pragma unroll
+        for (int k = i + 1; k < N; ++k) v -= L[pidx(k, i)] * b[k];
+        b[i] = v * inv_diag[i];
+    }
+}
+
+}  // namespace pv

@@ -1,0 +1,161 @@
+"""High-level handle over the C ABI, with PyTorch owning device memory and streams.
+
+    import torch, paper_2606_03989_gb300 as pv
+    trk = pv.Tracker((fx, fy, cx, cy, W, H), pv.params(kf_interval=10))
+    trk.track(frame0_cuda, normals0_cuda)          # keyframe
+    trk.track(frame1_cuda, n_iters=20)             # target: 20 GBP sweeps
+    xi = trk.pose()                                # se(3) [theta; rho] vs keyframe
+    depth = trk.depth()                            # (H, W) float32 CUDA tensor
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as nat
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+class Tracker:
+    def __init__(self, K, params=None, device=None, stream=None):
+        import torch
+        self._torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("PixVOD needs a CUDA device; no CPU implementation exists")
+        if not isinstance(K, nat.pixvod_intrinsics):
+            K = nat.intrinsics(*K)
+        self.K = K
+        self.params = params if params is not None else nat.params_default()
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = nat.workspace_bytes(K, self.params)
+        # over-allocate so the workspace can be aligned to 256 bytes
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        nat.check(nat.lib.pixvod_create(ctypes.byref(K), ctypes.byref(self.params), self._ws_ptr, nbytes,
+                                        self.stream.cuda_stream, ctypes.byref(h)), "pixvod_create")
+        self._h = h
+
+    @property
+    def shape(self):
+        return (self.K.height, self.K.width)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            nat.lib.pixvod_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def _check_image(self, t, channels=1):
+        torch = self._torch
+        if t is None:
+            return None
+        shape = self.shape if channels == 1 else self.shape + (channels,)
+        if tuple(t.shape) != shape or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError("expected a contiguous float32 tensor of shape %s" % (shape,))
+        return t
+
+    def track(self, frame, normals=None, n_iters: int = 20):
+        """frame: (H, W) float32 CUDA tensor; normals: (H, W, 3) float32 CUDA tensor
+        when this frame becomes a keyframe."""
+        frame = self._check_image(frame)
+        normals = self._check_image(normals, 3)
+        nat.check(nat.lib.pixvod_track(self._h, _ptr(frame), _ptr(normals), int(n_iters)), "pixvod_track")
+
+    def track_host(self, frame, normals=None, n_iters: int = 20):
+        """Host inputs (pinned CPU tensors or numpy arrays); copies run inside the library."""
+        torch = self._torch
+        keep = []
+
+        def host_ptr(x, channels):
+            if x is None:
+                return 0
+            if isinstance(x, np.ndarray):
+                x = np.ascontiguousarray(x, dtype=np.float32)
+                keep.append(x)
+                return x.ctypes.data
+            self._check_image(x, channels)
+            if x.device.type != "cpu":
+                raise ValueError("track_host expects host memory")
+            keep.append(x)
+            return x.data_ptr()
+
+        st = nat.lib.pixvod_track_host(self._h, host_ptr(frame, 1), host_ptr(normals, 3), int(n_iters))
+        nat.check(st, "pixvod_track_host")
+        if any(isinstance(k, np.ndarray) for k in keep):
+            self.stream.synchronize()   # pageable numpy buffers must outlive the copies
+        return keep
+
+    def sweep(self, n_iters: int):
+        nat.check(nat.lib.pixvod_sweep(self._h, int(n_iters)), "pixvod_sweep")
+
+    def pose(self) -> np.ndarray:
+        xi = np.zeros(6)
+        nat.check(nat.lib.pixvod_get_pose(self._h, xi.ctypes.data), "pixvod_get_pose")
+        return xi
+
+    def pose_global(self) -> np.ndarray:
+        T = np.zeros(16)
+        nat.check(nat.lib.pixvod_get_pose_global(self._h, T.ctypes.data), "pixvod_get_pose_global")
+        return T.reshape(4, 4)
+
+    def pose_device(self, out=None):
+        torch = self._torch
+        out = out if out is not None else torch.empty(6, dtype=torch.float64, device=self.device)
+        nat.check(nat.lib.pixvod_get_pose_device(self._h, out.data_ptr()), "pixvod_get_pose_device")
+        return out
+
+    def depth(self, out=None):
+        torch = self._torch
+        out = out if out is not None else torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        nat.check(nat.lib.pixvod_get_depth(self._h, out.data_ptr()), "pixvod_get_depth")
+        return out
+
+    def inv_depth(self, out=None):
+        torch = self._torch
+        out = out if out is not None else torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        nat.check(nat.lib.pixvod_get_inv_depth(self._h, out.data_ptr()), "pixvod_get_inv_depth")
+        return out
+
+    def status(self) -> int:
+        flags = ctypes.c_uint32(0)
+        st = nat.lib.pixvod_get_status(self._h, ctypes.byref(flags))
+        if st not in (nat.OK, nat.ENUMERIC):
+            nat.check(st, "pixvod_get_status")
+        return flags.value
+
+    def save_state(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        nat.check(nat.lib.pixvod_state_size(self._h, ctypes.byref(n)), "pixvod_state_size")
+        buf = ctypes.create_string_buffer(n.value)
+        nat.check(nat.lib.pixvod_save_state(self._h, buf, n.value), "pixvod_save_state")
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        nat.check(nat.lib.pixvod_load_state(self._h, buf, len(blob)), "pixvod_load_state")
+        self.stream.synchronize()
+
+    def state(self) -> nat.StateView:
+        return nat.parse_state(self.save_state())
+
+    def set_profiling(self, enable: bool):
+        nat.check(nat.lib.pixvod_set_profiling(self._h, int(bool(enable))), "pixvod_set_profiling")
+
+    def profile(self) -> dict:
+        pr = nat.pixvod_profile()
+        nat.check(nat.lib.pixvod_get_profile(self._h, ctypes.byref(pr)), "pixvod_get_profile")
+        return {"sweep_launches": pr.sweep_launches, "sweep_ms": pr.sweep_ms,
+                "kernel_launches": pr.kernel_launches}
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int64(0)
+        nat.check(nat.lib.pixvod_launch_count(self._h, ctypes.byref(n)), "pixvod_launch_count")
+        return n.value

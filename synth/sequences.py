@@ -50,8 +50,10 @@ def _inv(T):
 class Sequence:
     """A camera moving through a static scene.
 
-    ``poses[k]`` is the camera-to-world pose of frame k. ``kf_interval`` and
-    ``sweeps`` are the tracking schedule the workload is run with.
+    ``poses[k]`` is the camera-to-world pose of frame k. ``kf_interval``,
+    ``sweeps`` and ``sigma_P`` are the tracking schedule and pose-prior strength
+    the workload is run with (the prior is the weakest one found not to diverge
+    early on that workload family, the selection rule of the paper's App. E.3).
     """
     name: str
     cam: Camera
@@ -63,6 +65,7 @@ class Sequence:
     dropout: float = 0.0
     sweeps: int = 20
     kf_interval: int = 10
+    sigma_P: float = 0.05
 
     def __post_init__(self):
         self._cache = {}
@@ -150,7 +153,7 @@ def tiny_pair(seed: int = 0) -> Sequence:
                 break
         if ok:
             return Sequence("tiny", cam, scene, poses, seed, noise_sigma=1.0 / 255.0,
-                            sweeps=50, kf_interval=1)
+                            sweeps=50, kf_interval=1, sigma_P=0.1)
     raise RuntimeError("tiny_pair: rejection sampling failed")
 
 
