@@ -1,0 +1,358 @@
+"""Benchmark: synchronous GBP sweeps of the PixVOD tracker at 640x480 on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--sweeps S]
+    python bench.py --impl reference ...      (the FP64 CPU oracle, bounded sample)
+
+One step is one frame through the whole path: frame ingest, S synchronous GBP
+sweeps (linearise, Schur messages, neighbour exchange, damped belief update),
+the pose reduction and, every 10th frame, the on-device keyframe anchoring.
+The workload is the realistic synthetic sequence (640x480, fx=fy=525,
+cx=319.5, cy=239.5, planar + sinusoidal surfaces, 8-bit quantised, 2/255 noise,
+1% dropout). Frames are rendered before the timed region and are resident in
+device memory; the state (2 x 183 MB) is larger than the 129 MB L2, so no flush
+is needed between steps. Under torchrun each rank tracks its own sequence
+(replicas; no data exchange) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W_IMG, H_IMG = 640, 480
+METRIC = "Mpixel*GBP-sweeps/s at 640x480"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_640x480_traffic.json")
+STATE_PLANES, INPUT_PLANES = 151, 6
+# algorithmic bytes per pixel per sweep (FP32): every state plane read once and
+# written once, plus the six input planes (I_s, I_t, g_x, g_y, m_x, m_y) read once
+BYTES_PER_PX_SWEEP = 4 * (2 * STATE_PLANES + INPUT_PLANES)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _render(args):
+    seed, k, n_frames, need_normals = args
+    import synth
+    seq = synth.realistic(seed, n_frames)
+    f = seq.frame(k)
+    n = seq.normals(k) if need_normals else None
+    return k, f, n
+
+
+def render_frames(seed, n_frames, kf_interval, procs):
+    """Frames 0..n_frames-1 (normals for keyframes), rendered by a spawn pool."""
+    import multiprocessing as mp
+    jobs = [(seed, k, n_frames, k % kf_interval == 0) for k in range(n_frames)]
+    if procs > 1:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            out = pool.map(_render, jobs)
+    else:
+        out = [_render(j) for j in jobs]
+    out.sort(key=lambda t: t[0])
+    return [o[1] for o in out], {o[0]: o[2] for o in out if o[2] is not None}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) == 8]
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("pv_kernels.cuh", "pv_math.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_03989_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """ncu DRAM bytes per sweep launch, if taken on the current kernel source."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(values, op, group_backend=None):
+    """Reduce a list of floats over ranks (max or sum); identity for one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return list(values)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor(values, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return t.cpu().tolist()
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (bounded sample of the same workload)
+# --------------------------------------------------------------------------
+def oracle_sample(frames, normals, sweeps, rows=(180, 300), cols=(0, W_IMG)):
+    """Time the FP64 oracle on a band of the workload's first target frame (by
+    default rows 180-300 at full width, a quarter of the image, with the whole
+    target image for the warps), ``sweeps`` sweeps from the keyframe reset.
+    Returns (Mpx*sweeps/s, seconds, pixels)."""
+    import synth
+    from oracle import factors as fac
+    from oracle import gbp
+    from oracle.factors import Intrinsics
+    from oracle.gbp import Params
+    f32 = lambda x: float(np.float32(x))  # noqa: E731
+    seq = synth.realistic(2, 1)
+    K = Intrinsics(*(f32(v) for v in seq.cam.as_tuple()[:4]), W_IMG, H_IMG)
+    p = Params(sigma_P=f32(seq.sigma_P), **{k: f32(getattr(Params(), k)) for k in
+                                            ("sigma_D", "sigma_R", "sigma_N", "sigma_Z", "t_huber", "damping")})
+    v0, v1 = rows
+    u0, u1 = cols
+    I_s = frames[0].astype(np.float64)
+    I_t = frames[1].astype(np.float64)
+    m_x, m_y = fac.normal_edge_measurements(normals[0].astype(np.float64), K)
+    g_x, g_y = fac.image_gradient(I_t)
+    win = gbp.Window(K, I_s[v0:v1, u0:u1], m_x[v0:v1, u0:u1 - 1], m_y[v0:v1 - 1, u0:u1], I_t, g_x, g_y,
+                     u0, v0, 0.0)
+    st = gbp.reset_state(win.shape, 0.0, p)
+    t0 = time.perf_counter()
+    for _ in range(sweeps):
+        st = gbp.sweep(win, st, p)
+    dt = time.perf_counter() - t0
+    npx = (v1 - v0) * (u1 - u0)
+    return npx * sweeps / dt / 1e6, dt, npx
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    frames, normals = render_frames(2, 2, 10, 1)
+    samples = []
+    for step in range(args.warmup + args.steps):
+        v, dt, npx = oracle_sample(frames, normals, 1, rows=(228, 252))
+        if step >= args.warmup:
+            samples.append((v, dt))
+    value = npx * args.steps / sum(dt for _, dt in samples) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpx*sweeps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(dt for _, dt in samples),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "realistic synthetic sequence 640x480 (bounded sample: a 24x640 band of "
+                               "the keyframe, one GBP sweep per step)", "sweeps_per_step": 1},
+        "cpu_baseline": {"value": value, "unit": "Mpx*sweeps/s", "cores": 1, "kind": "oracle",
+                         "sample": "24x640 band (rows 228-252) of the 640x480 workload's first target "
+                                   "frame, 1 sweep per step from the keyframe reset"},
+        "e2e": {"value": value, "unit": "Mpx*sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_gpu(args):
+    ws, rank, local = dist_setup()
+    n_frames = 1 + args.warmup + args.steps
+    seed = 2 + rank
+    procs = max(1, min(16, (os.cpu_count() or 2) // max(ws, 1)))
+    frames, normals = render_frames(seed, n_frames, 10, procs)   # before any CUDA call
+
+    import torch
+    import torch.distributed as dist
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    import paper_2606_03989_gb300 as pv
+    import synth
+    seq = synth.realistic(seed, 1)
+
+    d_frames = [torch.from_numpy(f).to(dev) for f in frames]
+    d_normals = {k: torch.from_numpy(n).to(dev) for k, n in normals.items()}
+    params = pv.params(precision=32, kf_interval=10, sigma_P=seq.sigma_P)
+    stream = torch.cuda.Stream(dev)
+    trk = pv.Tracker(seq.cam.as_tuple(), params, dev, stream=stream)
+
+    def step(k):
+        trk.track(d_frames[k], d_normals.get(k), n_iters=args.sweeps)
+
+    with torch.cuda.stream(stream):
+        step(0)
+        for k in range(1, 1 + args.warmup):
+            step(k)
+        stream.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(local)
+        clocks.start()
+        trk.set_profiling(True)
+        n0 = trk.launch_count()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for k in range(1 + args.warmup, n_frames):
+            step(k)
+        ev1.record(stream)
+        ev1.synchronize()
+        launches = trk.launch_count() - n0
+        prof = trk.profile()
+        trk.set_profiling(False)
+        ck = clocks.stop()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    flags = trk.status()
+    # end to end through the public API with host buffers: pinned frame copy in,
+    # xi_est read back every step
+    h_frames = [torch.from_numpy(f).pin_memory() for f in frames]
+    h_normals = {k: torch.from_numpy(n).pin_memory() for k, n in normals.items()}
+    trk2 = pv.Tracker(seq.cam.as_tuple(), params, dev, stream=stream)
+    with torch.cuda.stream(stream):
+        for k in range(0, 1 + args.warmup):
+            trk2.track_host(h_frames[k], h_normals.get(k), n_iters=args.sweeps)
+            trk2.pose()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h2d = 0
+        for k in range(1 + args.warmup, n_frames):
+            trk2.track_host(h_frames[k], h_normals.get(k), n_iters=args.sweeps)
+            trk2.pose()
+            h2d += h_frames[k].numel() * 4 + (h_normals[k].numel() * 4 if k in h_normals else 0)
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - t0
+
+    px = W_IMG * H_IMG
+    ms_max, e2e_max = aggregate([ms, e2e_s], "max")
+    units = aggregate([float(px * args.sweeps * args.steps)], "sum")[0]
+    value = units / (ms_max * 1e-3) / 1e6
+    e2e_value = units / e2e_max / 1e6
+    if ws > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+
+    sweep_ms = prof["sweep_ms"] / max(prof["sweep_launches"], 1)
+    peak, peak_kind = hbm_peak()
+    achieved = px * BYTES_PER_PX_SWEEP / (sweep_ms * 1e-3) / 1e9
+    cpu_v, cpu_dt, cpu_px = oracle_sample(frames, normals, 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpx*sweeps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": "realistic synthetic sequence 640x480 (fx=fy=525), %d GBP sweeps per frame, "
+                        "keyframe every 10 frames" % args.sweeps,
+            "sweeps_per_frame": args.sweeps, "frames_per_s": ws * args.steps / (ms_max * 1e-3),
+            "parallelism": "replicas x%d" % ws if ws > 1 else "single GPU",
+            "l2": "no flush: the swept state (2 x %.0f MB) exceeds the 129 MB L2"
+                  % (STATE_PLANES * 4 * px / 1e6),
+            "device_flags": flags,
+        },
+        "roofline": {
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": measured_traffic(), "kernel": "k_sweep<float>", "peak_source": peak_kind,
+            "bytes_per_launch": px * BYTES_PER_PX_SWEEP, "sweep_ms": sweep_ms,
+        },
+        "cpu_baseline": {
+            "value": cpu_v, "unit": "Mpx*sweeps/s", "cores": 1, "kind": "oracle",
+            "sample": "FP64 oracle (numpy, one thread), rows 180-300 at full width (%d pixels, a "
+                      "quarter of the frame) of the workload's first target frame, 1 sweep from the "
+                      "keyframe reset (%.1f s)" % (cpu_px, cpu_dt),
+        },
+        "e2e": {"value": e2e_value, "unit": "Mpx*sweeps/s", "h2d_bytes_per_step": h2d / args.steps,
+                "d2h_bytes_per_step": 48},
+        "gpu_launches": launches,
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--sweeps", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    from paper_2606_03989_gb300 import build
+    build.build()
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
