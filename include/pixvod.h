@@ -204,6 +204,33 @@ pixvod_status pixvod_get_profile(pixvod_handle* h, pixvod_profile* out);
 /* Number of kernels this handle has launched since creation. */
 pixvod_status pixvod_launch_count(pixvod_handle* h, int64_t* out);
 
+/* Pose average without any device allocation. The paper has no counterpart: this
+ * is a library convenience for callers that cannot allocate device memory, such
+ * as code that runs while a CUDA stream is being captured, a real-time loop that
+ * forbids allocation after start-up, or a plugin whose host framework owns all
+ * device memory and offers it no workspace. It computes the same seven means as
+ * the tracker's own reduction (xi_est[0..5] and the mean log-depth, in row order
+ * with double accumulation) from caller-provided planes, using scratch held in a
+ * static device array of the library instead of a workspace.
+ *   d_mu: 7 float32 planes (xi_0..xi_5, log-depth) of height rows of `pitch`
+ *         elements, `plane_stride` elements apart (the checkpoint plane layout);
+ *   d_out: 7 doubles of device memory (the means); stream: a cudaStream_t.
+ * Limits and behaviour: height at most PIXVOD_STATIC_MAX_ROWS (4096); larger
+ * heights return EINVAL without touching the device. The static scratch
+ * (4096 x 7 doubles + a counter, about 229 KB) is held by every GPU that loads
+ * the library until the process exits. The first call on a device resolves the
+ * scratch's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture. Every call on a device shares the
+ * same scratch: calls whose kernels overlap on the GPU (different streams, no
+ * ordering between them) race and give wrong results. The call clears the part
+ * of the scratch that must start at zero (an asynchronous cudaMemsetAsync on the
+ * stream) and then launches one kernel; it calls no cudaMalloc or cudaFree.
+ * EINVAL on null or misaligned pointers, pitch < width, plane_stride <
+ * pitch * height or a height out of range; ECUDA on a CUDA error. */
+#define PIXVOD_STATIC_MAX_ROWS 4096
+pixvod_status pixvod_pose_mean_static(const float* d_mu, int32_t width, int32_t height, int64_t pitch,
+                                      int64_t plane_stride, double* d_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

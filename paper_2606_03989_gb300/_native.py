@@ -77,6 +77,7 @@ def _load():
         "pixvod_set_profiling": (S, [H, I32]),
         "pixvod_get_profile": (S, [H, ctypes.POINTER(pixvod_profile)]),
         "pixvod_launch_count": (S, [H, ctypes.POINTER(I64)]),
+        "pixvod_pose_mean_static": (S, [P, I32, I32, I64, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -28,7 +28,7 @@ def nvcc_path() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, "pixvod.cu")]
+    return [os.path.join(CSRC, "pixvod.cu"), os.path.join(CSRC, "pixvod_static.cu")]
 
 
 def build(verbose_ptxas: bool = False, force: bool = False) -> str:
