@@ -21,7 +21,6 @@ namespace {
 
 constexpr int kPitchAlign = 32;       // elements per row rounded up to 32
 constexpr size_t kAlign = 256;        // every workspace region starts on 256 bytes
-constexpr int kReduceBlocks = 304;    // 2 x 152 SMs
 constexpr int kProfilePairs = 4096;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -79,7 +78,7 @@ Layout make_layout(const pixvod_intrinsics* K, const pixvod_params* p) {
     L.off_stage_normals = off;
     off += align_up(npx * 3 * sizeof(float), kAlign);
     L.off_partials = off;
-    off += align_up(kReduceBlocks * 7 * sizeof(double), kAlign);
+    off += align_up((size_t)K->height * 7 * sizeof(double), kAlign);  // one partial per row
     L.off_scalars = off;
     off += align_up(sizeof(Scalars), kAlign);
     L.total = off;
@@ -155,6 +154,18 @@ dim3 pixel_block() { return dim3(32, 4); }
 dim3 pixel_grid(const pixvod_handle* h) {
     return dim3((h->K.width + 31) / 32, (h->K.height + 3) / 4);
 }
+dim3 sweep_block() { return dim3(pv::SWEEP_BX, pv::SWEEP_BY); }
+dim3 sweep_grid(const pixvod_handle* h) {
+    return dim3((h->K.width + pv::SWEEP_BX - 1) / pv::SWEEP_BX, (h->K.height + pv::SWEEP_BY - 1) / pv::SWEEP_BY);
+}
+
+// dynamic shared memory of the sweep kernel (above the 48 KB default for double)
+template <typename T>
+cudaError_t sweep_attributes() {
+    static cudaError_t once = cudaFuncSetAttribute(pv::k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)pv::sweep_smem_bytes<T>());
+    return once;
+}
 
 pixvod_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return PIXVOD_OK;
@@ -182,6 +193,8 @@ void harvest_profile(pixvod_handle* h) {
 
 template <typename T>
 pixvod_status run_sweeps(pixvod_handle* h, int n) {
+    pixvod_status st = cuda_status(sweep_attributes<T>());
+    if (st != PIXVOD_OK) return st;
     pv::SweepArgs<T> a;
     a.g = geometry<T>(h);
     a.f = factors<T>(h);
@@ -200,7 +213,7 @@ pixvod_status run_sweeps(pixvod_handle* h, int n) {
             if (h->ev_used == kProfilePairs) harvest_profile(h);
             cudaEventRecord(h->ev[2 * h->ev_used], h->stream);
         }
-        pv::k_sweep<T><<<pixel_grid(h), pixel_block(), 0, h->stream>>>(a);
+        pv::k_sweep<T><<<sweep_grid(h), sweep_block(), pv::sweep_smem_bytes<T>(), h->stream>>>(a);
         pixvod_status s = launched(h);
         if (prof) {
             cudaEventRecord(h->ev[2 * h->ev_used + 1], h->stream);
@@ -214,7 +227,7 @@ pixvod_status run_sweeps(pixvod_handle* h, int n) {
 
 template <typename T>
 pixvod_status run_reduce(pixvod_handle* h, int anchor) {
-    pv::k_reduce<T><<<kReduceBlocks, pv::RED_THREADS, 0, h->stream>>>(
+    pv::k_reduce<T><<<h->K.height, pv::RED_THREADS, 0, h->stream>>>(
         geometry<T>(h), state_ptr<T>(h, h->cur), reinterpret_cast<double*>(h->ws + h->L.off_partials),
         scalars(h), anchor);
     return launched(h);

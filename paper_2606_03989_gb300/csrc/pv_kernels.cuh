@@ -162,15 +162,33 @@ __device__ __forceinline__ T bilinear(const T* __restrict__ img, int pitch, int 
     return (T(1) - ay) * ((T(1) - ax) * a + ax * b) + ay * ((T(1) - ax) * c + ax * d);
 }
 
+// Thread block of the sweep kernel: 32 x SWEEP_BY pixels, one thread per pixel
+// (32 x 4 with at least 3 blocks per SM measured fastest on GB300).
+// Each thread keeps the four damped messages it produces in shared memory until
+// the belief solve has given tau (they are then projected and written), so the
+// direction loop is not unrolled and the register footprint stays moderate.
+constexpr int SWEEP_BX = 32;
+constexpr int SWEEP_BY = 4;
+constexpr int SWEEP_THREADS = SWEEP_BX * SWEEP_BY;
+constexpr int MSG_WORDS = 4 * (ID_STRIDE + 2);  // per thread: 4 x (27 identity + 2 normal)
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_sweep(const SweepArgs<T> a) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = blockIdx.y * blockDim.y + threadIdx.y;
+constexpr size_t sweep_smem_bytes() {
+    return sizeof(T) * MSG_WORDS * SWEEP_THREADS;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* msg = reinterpret_cast<T*>(smem_raw);  // msg[w * SWEEP_THREADS + tid]
+    const int tid = threadIdx.y * SWEEP_BX + threadIdx.x;
+    const int u = blockIdx.x * SWEEP_BX + threadIdx.x;
+    const int v = blockIdx.y * SWEEP_BY + threadIdx.y;
     const Geometry<T>& g = a.g;
     const Factors<T>& F = a.f;
     if (u >= g.W || v >= g.H) return;
-    const size_t PS = g.plane;
-    const size_t i = (size_t)v * g.pitch + u;
+    const int PS = (int)g.plane;
+    const int i = v * g.pitch + u;
     const T* __restrict__ S = a.in;
     T* __restrict__ D = a.out;
 
@@ -205,7 +223,7 @@ __global__ void __launch_bounds__(128) k_sweep(const SweepArgs<T> a) {
         Xt[2] += t[2];
         T Z = Xt[2];
         bool valid = Z > T(1e-6);
-        T iz = valid ? T(1) / Z : T(0);
+        T iz = valid ? v_div(T(1), Z) : T(0);
         T x = g.fx * Xt[0] * iz + g.cx;
         T y = g.fy * Xt[1] * iz + g.cy;
         // overlap test with a 1e-3 px margin (pixels warped by the identity land on
@@ -259,43 +277,52 @@ __global__ void __launch_bounds__(128) k_sweep(const SweepArgs<T> a) {
     eb[6] -= F.lam_Z * (d - T(a.sc->d_prior));
 
     // --- a2/a3: pairwise messages from the four neighbours ---
-    T Mk[4][27];
-    T Nk[4][2];
     unsigned flags = 0;
-#pragma unroll
+    const T beta = F.beta, omb = T(1) - F.beta;
+#pragma unroll 1
     for (int k = 0; k < 4; ++k) {
+        T* mb = msg + (k * (ID_STRIDE + 2)) * SWEEP_THREADS + tid;
         const int un = u + (k == 0 ? -1 : (k == 1 ? 1 : 0));
         const int vn = v + (k == 2 ? -1 : (k == 3 ? 1 : 0));
         const bool has = un >= 0 && un < g.W && vn >= 0 && vn < g.H;
         if (!has) {
 #pragma unroll
-            for (int q = 0; q < 27; ++q) Mk[k][q] = T(0);
-            Nk[k][0] = T(0);
-            Nk[k][1] = T(0);
+            for (int q = 0; q < ID_STRIDE + 2; ++q) mb[q * SWEEP_THREADS] = T(0);
             continue;
         }
-        const size_t j = (size_t)vn * g.pitch + un;
+        const int j = vn * g.pitch + un;
         const int ko = k ^ 1;
+        const T* Sj = S + j;
+        const T* Si = S + i;
         // identity factor (Eq. 5): r = Log(Exp(xi_j)^-1 Exp(xi_i)), J_i = I, J_j = -I
-        T xj[6];
+        T rb[6];
+        {
+            T xj[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) xj[q] = S[q * PS + j];
-        T Rj[9], tj[3], Rr[9], tr[3], rb[6];
-        se3_exp(xj, Rj, tj);
-        se3_invmul(Rj, tj, R, t, Rr, tr);
-        se3_log(Rr, tr, rb);
+            for (int q = 0; q < 6; ++q) xj[q] = Sj[q * PS];
+            T Rj[9], tj[3], Rr[9], tr[3];
+            se3_exp(xj, Rj, tj);
+            se3_invmul(Rj, tj, R, t, Rr, tr);
+            se3_log(Rr, tr, rb);
+        }
         // variable-to-factor marginal of j: V = W + u u^T with W = M_p,j - Lambda_{f->j}
         // (pose prior plus j's three other identity messages) and u = u_j
-        T W[21], C[21], ev[6], uj[6];
+        const T* mj = Sj + (PL_ID + ID_STRIDE * ko) * PS;
+        T W[21], C[21], uj[6], gv[6];
 #pragma unroll
         for (int q = 0; q < 21; ++q) {
-            W[q] = S[(PL_MP + q) * PS + j] - S[(PL_ID + ID_STRIDE * ko + q) * PS + j];
+            W[q] = Sj[(PL_MP + q) * PS] - mj[q * PS];
             C[q] = W[q];
         }
 #pragma unroll
+        for (int q = 0; q < 6; ++q) uj[q] = Sj[(PL_U + q) * PS];
+        // g0 = eta_v - W r with eta_v = -eta_{f->j}
+#pragma unroll
         for (int q = 0; q < 6; ++q) {
-            ev[q] = -S[(PL_ID + ID_STRIDE * ko + 21 + q) * PS + j];
-            uj[q] = S[(PL_U + q) * PS + j];
+            T wr = T(0);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) wr += W[pidx(q, c)] * rb[c];
+            gv[q] = -mj[(21 + q) * PS] - wr;
         }
         // A = W + lam_R I is well conditioned (W is bounded by a few lam_R)
 #pragma unroll
@@ -304,22 +331,9 @@ __global__ void __launch_bounds__(128) k_sweep(const SweepArgs<T> a) {
         if (!chol_packed<6>(C, idg)) flags |= FLAG_NONPOS_PIVOT;
         // Lambda_msg = lam_R C^-1 V with C = A + u u^T:
         //   = W - (L^-1 W)^T (L^-1 W) + lam_R^2 / (1 + u^T z) z z^T,  z = A^-1 u
-        T Y[6][6];
+        T z[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-#pragma unroll
-            for (int r = 0; r < 6; ++r) Y[c][r] = W[pidx(r, c)];
-            fwd_solve<6>(C, idg, Y[c]);
-        }
-        T z[6], gv[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            z[q] = uj[q];
-            T wr = T(0);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) wr += W[pidx(q, c)] * rb[c];
-            gv[q] = ev[q] - wr;  // g0 = eta_v - W r
-        }
+        for (int q = 0; q < 6; ++q) z[q] = uj[q];
         fwd_solve<6>(C, idg, z);
         bwd_solve<6>(C, idg, z);
         fwd_solve<6>(C, idg, gv);
@@ -331,48 +345,54 @@ __global__ void __launch_bounds__(128) k_sweep(const SweepArgs<T> a) {
             ur += uj[q] * rb[q];
             uh += uj[q] * gv[q];
         }
-        const T iuz = T(1) / (T(1) + uz);
+        const T iuz = v_div(T(1), T(1) + uz);
         const T crank = F.lam_R * F.lam_R * iuz;
         // eta_msg = lam_R C^-1 (eta_v - V r) = lam_R (h - z (u^T r + u^T h) / (1 + u^T z))
         const T ecoef = (ur + uh) * iuz;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) gv[q] -= ecoef * z[q];
-        const T beta = F.beta, omb = T(1) - F.beta;
-#pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-            for (int c = 0; c <= r; ++c) {
-                T yy = T(0);
-#pragma unroll
-                for (int q = 0; q < 6; ++q) yy += Y[r][q] * Y[c][q];
-                T lnew = W[pidx(r, c)] - yy + crank * z[r] * z[c];
-                T lold = S[(PL_ID + ID_STRIDE * k + pidx(r, c)) * PS + i];
-                Mk[k][pidx(r, c)] = omb * lnew + beta * lold;
-            }
+        const T* mi = Si + (PL_ID + ID_STRIDE * k) * PS;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-            T eold = S[(PL_ID + ID_STRIDE * k + 21 + q) * PS + i];
-            Mk[k][21 + q] = omb * (F.lam_R * gv[q]) + beta * eold;
+            T e = omb * (F.lam_R * (gv[q] - ecoef * z[q])) + beta * mi[(21 + q) * PS];
+            eb[q] += e;
+            mb[(21 + q) * SWEEP_THREADS] = e;
         }
+        // Y = L^-1 W in place of W (columns), then Lambda = W - Y^T Y + crank z z^T
+        {
+            T Y[6][6];
 #pragma unroll
-        for (int q = 0; q < 21; ++q) Mp[q] += Mk[k][q];
+            for (int c = 0; c < 6; ++c) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) eb[q] += Mk[k][21 + q];
+                for (int r = 0; r < 6; ++r) Y[c][r] = W[pidx(r, c)];
+                fwd_solve<6>(C, idg, Y[c]);
+            }
+#pragma unroll
+            for (int r = 0; r < 6; ++r)
+#pragma unroll
+                for (int c = 0; c <= r; ++c) {
+                    T yy = T(0);
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) yy += Y[r][q] * Y[c][q];
+                    T lnew = W[pidx(r, c)] - yy + crank * z[r] * z[c];
+                    T l = omb * lnew + beta * mi[pidx(r, c) * PS];
+                    Mp[pidx(r, c)] += l;
+                    mb[pidx(r, c) * SWEEP_THREADS] = l;
+                }
+        }
 
         // normal-integration factor (Eq. 6): r_i = d_i - d_j + sg m
-        T dj = S[6 * PS + j];
-        T sv = S[PL_S * PS + j] - S[(PL_NM + 2 * ko) * PS + j];
-        T evn = -S[(PL_NM + 2 * ko + 1) * PS + j];
+        T dj = Sj[6 * PS];
+        T sv = Sj[PL_S * PS] - Sj[(PL_NM + 2 * ko) * PS];
+        T evn = -Sj[(PL_NM + 2 * ko + 1) * PS];
         T m = k == 0 ? a.m_x[i - 1] : (k == 1 ? a.m_x[i] : (k == 2 ? a.m_y[i - g.pitch] : a.m_y[i]));
         T sg = (k == 0 || k == 2) ? T(1) : T(-1);
         T rn = d - dj + sg * m;
-        T den = T(1) / (F.lam_N + sv);
-        T nnew = F.lam_N * sv * den;
-        T enew = F.lam_N * (evn - sv * rn) * den;
-        Nk[k][0] = omb * nnew + beta * S[(PL_NM + 2 * k) * PS + i];
-        Nk[k][1] = omb * enew + beta * S[(PL_NM + 2 * k + 1) * PS + i];
-        md += Nk[k][0];
-        eb[6] += Nk[k][1];
+        T den = v_div(T(1), F.lam_N + sv);
+        T nnew = omb * (F.lam_N * sv * den) + beta * Si[(PL_NM + 2 * k) * PS];
+        T enew = omb * (F.lam_N * (evn - sv * rn) * den) + beta * Si[(PL_NM + 2 * k + 1) * PS];
+        md += nnew;
+        eb[6] += enew;
+        mb[ID_STRIDE * SWEEP_THREADS] = nnew;
+        mb[(ID_STRIDE + 1) * SWEEP_THREADS] = enew;
     }
 
     // --- a4: belief, mean update, tangent projection ---
@@ -382,34 +402,39 @@ __global__ void __launch_bounds__(128) k_sweep(const SweepArgs<T> a) {
     //   P = M_p + u u^T,  u = sqrt(alpha m_d / (m_d + alpha J_d^2)) J_p,
     //   s = m_d + alpha J_d^2 / (1 + alpha q),
     // all free of cancellation.
-    T Lp[21], idp[6];
-#pragma unroll
-    for (int q = 0; q < 21; ++q) Lp[q] = Mp[q];
-    bool ok = chol_packed<6>(Lp, idp);
-    T up[6], gp[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        up[q] = J[q];
-        gp[q] = eb[q];
-    }
-    fwd_solve<6>(Lp, idp, up);
-    bwd_solve<6>(Lp, idp, up);
-    fwd_solve<6>(Lp, idp, gp);
-    bwd_solve<6>(Lp, idp, gp);
-    T qv = T(0), jh = T(0);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        qv += J[q] * up[q];
-        jh += J[q] * gp[q];
-    }
-    const T imd = T(1) / md;
-    const T hd = eb[6] * imd;
-    const T zd = J[6] * imd;
-    const T coef = alpha * (rph + jh + J[6] * hd) / (T(1) + alpha * (qv + J[6] * zd));
     T tau[7];
+    T qv;
+    bool ok;
+    {
+        T Lp[21], idp[6];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) tau[q] = gp[q] - coef * up[q];
-    tau[6] = hd - coef * zd;
+        for (int q = 0; q < 21; ++q) Lp[q] = Mp[q];
+        ok = chol_packed<6>(Lp, idp);
+        T up[6], gp[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            up[q] = J[q];
+            gp[q] = eb[q];
+        }
+        fwd_solve<6>(Lp, idp, up);
+        bwd_solve<6>(Lp, idp, up);
+        fwd_solve<6>(Lp, idp, gp);
+        bwd_solve<6>(Lp, idp, gp);
+        T jh = T(0);
+        qv = T(0);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            qv += J[q] * up[q];
+            jh += J[q] * gp[q];
+        }
+        const T imd = v_div(T(1), md);
+        const T hd = eb[6] * imd;
+        const T zd = J[6] * imd;
+        const T coef = v_div(alpha * (rph + jh + J[6] * hd), T(1) + alpha * (qv + J[6] * zd));
+#pragma unroll
+        for (int q = 0; q < 6; ++q) tau[q] = gp[q] - coef * up[q];
+        tau[6] = hd - coef * zd;
+    }
     bool fin = true;
 #pragma unroll
     for (int q = 0; q < 7; ++q) fin = fin && v_finite(tau[q]);
@@ -419,6 +444,7 @@ __global__ void __launch_bounds__(128) k_sweep(const SweepArgs<T> a) {
 #pragma unroll
         for (int q = 0; q < 7; ++q) tau[q] = T(0);
     }
+    T* Di = D + i;
     // mu <- mu (+) tau
     {
         T Rt[9], tt[3], Rn[9], tn[3], xn[6];
@@ -426,32 +452,39 @@ __global__ void __launch_bounds__(128) k_sweep(const SweepArgs<T> a) {
         se3_mul(R, t, Rt, tt, Rn, tn);
         se3_log(Rn, tn, xn);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) D[q * PS + i] = xn[q];
-        D[6 * PS + i] = d + tau[6];
+        for (int q = 0; q < 6; ++q) Di[q * PS] = xn[q];
+        Di[6 * PS] = d + tau[6];
     }
     {
-        const T bp = alpha * md / (md + alpha * J[6] * J[6]);
+        const T bp = v_div(alpha * md, md + alpha * J[6] * J[6]);
         const T sb = v_sqrt(bp);
 #pragma unroll
-        for (int q = 0; q < 21; ++q) D[(PL_MP + q) * PS + i] = Mp[q];
+        for (int q = 0; q < 21; ++q) Di[(PL_MP + q) * PS] = Mp[q];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) D[(PL_U + q) * PS + i] = sb * J[q];
-        D[PL_S * PS + i] = md + alpha * J[6] * J[6] / (T(1) + alpha * qv);
+        for (int q = 0; q < 6; ++q) Di[(PL_U + q) * PS] = sb * J[q];
+        Di[PL_S * PS] = md + v_div(alpha * J[6] * J[6], T(1) + alpha * qv);
     }
     // messages, projected: eta <- eta - Lambda tau
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < 4; ++k) {
+        const T* mb = msg + (k * (ID_STRIDE + 2)) * SWEEP_THREADS + tid;
+        T* dk = Di + (PL_ID + ID_STRIDE * k) * PS;
+        T L[21];
 #pragma unroll
-        for (int q = 0; q < 21; ++q) D[(PL_ID + ID_STRIDE * k + q) * PS + i] = Mk[k][q];
+        for (int q = 0; q < 21; ++q) {
+            L[q] = mb[q * SWEEP_THREADS];
+            dk[q * PS] = L[q];
+        }
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
-            T s = Mk[k][21 + r];
+            T e = mb[(21 + r) * SWEEP_THREADS];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) s -= Mk[k][pidx(r, c)] * tau[c];
-            D[(PL_ID + ID_STRIDE * k + 21 + r) * PS + i] = s;
+            for (int c = 0; c < 6; ++c) e -= L[pidx(r, c)] * tau[c];
+            dk[(21 + r) * PS] = e;
         }
-        D[(PL_NM + 2 * k) * PS + i] = Nk[k][0];
-        D[(PL_NM + 2 * k + 1) * PS + i] = Nk[k][1] - Nk[k][0] * tau[6];
+        T n = mb[ID_STRIDE * SWEEP_THREADS];
+        Di[(PL_NM + 2 * k) * PS] = n;
+        Di[(PL_NM + 2 * k + 1) * PS] = mb[(ID_STRIDE + 1) * SWEEP_THREADS] - n * tau[6];
     }
     if (flags) atomicOr(&a.sc->flags, flags);
 }
@@ -461,6 +494,10 @@ __global__ void __launch_bounds__(128) k_sweep(const SweepArgs<T> a) {
 // ---------------------------------------------------------------------------
 constexpr int RED_THREADS = 256;
 
+// One block per image row sums that row's 7 mean planes (double accumulation,
+// fixed order); the last block to finish sums the row partials in row order,
+// writes xi_est and the mean log-depth, composes T_cur = Exp(xi_est) T_kf and,
+// at an anchoring frame, moves the keyframe: T_kf <- T_cur, d_prior <- d_mean.
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_reduce(Geometry<T> g, const T* __restrict__ state,
                                                         double* __restrict__ partials, Scalars* sc,
@@ -468,14 +505,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(Geometry<T> g, const T* 
     __shared__ double sh[7][RED_THREADS];
     __shared__ bool last;
     const int tid = threadIdx.x;
-    const size_t n = (size_t)g.W * g.H;
+    const int row = blockIdx.x;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (size_t p = (size_t)blockIdx.x * RED_THREADS + tid; p < n; p += (size_t)gridDim.x * RED_THREADS) {
-        size_t v = p / g.W, u = p - v * g.W;
-        size_t i = v * g.pitch + u;
+    const T* base = state + (size_t)row * g.pitch;
+    for (int u = tid; u < g.W; u += RED_THREADS)
 #pragma unroll
-        for (int q = 0; q < 7; ++q) acc[q] += double(state[q * g.plane + i]);
-    }
+        for (int q = 0; q < 7; ++q) acc[q] += double(base[q * g.plane + u]);
 #pragma unroll
     for (int q = 0; q < 7; ++q) sh[q][tid] = acc[q];
     __syncthreads();
@@ -487,34 +522,40 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(Geometry<T> g, const T* 
     }
     if (tid == 0) {
 #pragma unroll
-        for (int q = 0; q < 7; ++q) partials[blockIdx.x * 7 + q] = sh[q][0];
+        for (int q = 0; q < 7; ++q) partials[row * 7 + q] = sh[q][0];
         __threadfence();
-        unsigned ticket = atomicAdd(&sc->counter, 1u);
-        last = ticket == gridDim.x - 1;
+        last = atomicAdd(&sc->counter, 1u) == (unsigned)(gridDim.x - 1);
     }
     __syncthreads();
     if (!last) return;
-    // the last block sums the partials in block order
-    if (tid < 7) {
-        double s = 0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(partials + b * 7 + tid);
-        sh[tid][0] = s / double(n);
-    }
+    double r[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int h = tid; h < (int)gridDim.x; h += RED_THREADS)
+#pragma unroll
+        for (int q = 0; q < 7; ++q) r[q] += __ldcg(partials + h * 7 + q);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) sh[q][tid] = r[q];
     __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (tid < s)
+#pragma unroll
+            for (int q = 0; q < 7; ++q) sh[q][tid] += sh[q][tid + s];
+        __syncthreads();
+    }
     if (tid == 0) {
+        const double n = double(g.W) * double(g.H);
         double xi[6], R[9], t[3];
         for (int q = 0; q < 6; ++q) {
-            xi[q] = sh[q][0];
+            xi[q] = sh[q][0] / n;
             sc->xi_est[q] = xi[q];
         }
-        sc->d_mean = sh[6][0];
+        sc->d_mean = sh[6][0] / n;
         se3_exp(xi, R, t);
         // T_cur = Exp(xi_est) T_kf with Exp(xi_est) = [R t; 0 1]
         double Tc[16];
         for (int c = 0; c < 4; ++c) {
-            for (int r = 0; r < 3; ++r)
-                Tc[4 * r + c] = R[3 * r] * sc->T_kf[c] + R[3 * r + 1] * sc->T_kf[4 + c] +
-                                R[3 * r + 2] * sc->T_kf[8 + c] + t[r] * sc->T_kf[12 + c];
+            for (int r2 = 0; r2 < 3; ++r2)
+                Tc[4 * r2 + c] = R[3 * r2] * sc->T_kf[c] + R[3 * r2 + 1] * sc->T_kf[4 + c] +
+                                 R[3 * r2 + 2] * sc->T_kf[8 + c] + t[r2] * sc->T_kf[12 + c];
             Tc[12 + c] = sc->T_kf[12 + c];
         }
         for (int q = 0; q < 16; ++q) sc->T_cur[q] = Tc[q];

@@ -31,20 +31,34 @@ __device__ __forceinline__ void v_sincos(float x, float* s, float* c) { sincosf(
 __device__ __forceinline__ void v_sincos(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ bool v_finite(float x) { return isfinite(x); }
 __device__ __forceinline__ bool v_finite(double x) { return isfinite(x); }
+// reciprocal square root and quotient: the float path uses the approximate
+// hardware forms (a few ulp), the double (verification) path the exact ones
+__device__ __forceinline__ float v_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double v_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float v_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double v_div(double a, double b) { return a / b; }
 
 // Precision-dependent series limits: below `tiny` the A/B quotients use two
 // Taylor terms; below 1 rad the C and D coefficients use their power series
 // with enough terms for the type's epsilon.
 template <typename T> struct Prec;
+// Float: below ab_series_max = 0.3 rad, A and B use their power series to t^6
+// (truncation below 2e-10) and the logarithm recovers the angle from
+// s = sin(t) with the arcsine series to s^9 when s < 0.2 and cos(t) > 0
+// (truncation below 5e-10), so small rotations need no trigonometric calls.
 template <> struct Prec<float> {
     static constexpr float tiny = 1e-4f;
     static constexpr int c_terms = 7;
     static constexpr float d_series_max = 1.0f;
+    static constexpr float ab_series_max = 0.3f;
+    static constexpr float asin_series_max = 0.2f;
 };
 template <> struct Prec<double> {
     static constexpr double tiny = 1e-8;
     static constexpr int c_terms = 12;
     static constexpr double d_series_max = 0.5;
+    static constexpr double ab_series_max = 1e-8;
+    static constexpr double asin_series_max = 0.0;
 };
 
 // (t - sin t)/t^3 = sum_k (-1)^k t^(2k) / (2k+3)!
@@ -71,7 +85,12 @@ __device__ __forceinline__ T series_D(T t2) {
 
 template <typename T>
 __device__ __forceinline__ void coef_AB(T t, T* A, T* B) {
-    if (t < Prec<T>::tiny) {
+    if (t < Prec<T>::ab_series_max) {
+        // sin t / t = 1 - t^2/3! + t^4/5! - t^6/7!; (1 - cos t)/t^2 = 1/2! - t^2/4! + t^4/6! - t^6/8!
+        T t2 = t * t;
+        *A = T(1) - t2 * (T(1) / T(6) - t2 * (T(1) / T(120) - t2 * (T(1) / T(5040))));
+        *B = T(0.5) - t2 * (T(1) / T(24) - t2 * (T(1) / T(720) - t2 * (T(1) / T(40320))));
+    } else if (t < Prec<T>::tiny) {
         T t2 = t * t;
         *A = T(1) - t2 / T(6);
         *B = T(0.5) - t2 / T(24);
@@ -157,7 +176,14 @@ __device__ __forceinline__ void se3_log(const T* R, const T* t, T* xi) {
     T w2 = T(0.5) * (R[3] - R[1]);
     T s = v_sqrt(w0 * w0 + w1 * w1 + w2 * w2);
     T c = T(0.5) * (R[0] + R[4] + R[8] - T(1));
-    T th = v_atan2(s, c);
+    T th;
+    if (s < Prec<T>::asin_series_max && c > T(0)) {
+        // asin s = s + s^3/6 + 3 s^5/40 + 5 s^7/112 + 35 s^9/1152
+        T s2 = s * s;
+        th = s * (T(1) + s2 * (T(1) / T(6) + s2 * (T(3) / T(40) + s2 * (T(5) / T(112) + s2 * (T(35) / T(1152))))));
+    } else {
+        th = v_atan2(s, c);
+    }
     T A, B;
     coef_AB(th, &A, &B);
     T inv = T(1) / A;
@@ -208,8 +234,8 @@ __device__ __forceinline__ bool chol_packed(T* A, T* inv_diag) {
 #pragma unroll
         for (int k = 0; k < j; ++k) d -= A[pidx(j, k)] * A[pidx(j, k)];
         ok = ok && (d > T(0));
-        T ljj = v_sqrt(d > T(0) ? d : T(1));
-        T inv = T(1) / ljj;
+        T inv = v_rsqrt(d > T(0) ? d : T(1));
+        T ljj = (d > T(0) ? d : T(1)) * inv;
         A[pidx(j, j)] = ljj;
         inv_diag[j] = inv;
 #pragma unroll
