@@ -188,9 +188,10 @@ pixvod_status pixvod_get_status(pixvod_handle* h, uint32_t* flags);
  * m_y (to the lower neighbour).
  * Scalars (doubles): xi_est[6], T_kf[16] (T_kf<-world), T_cur[16], d_prior,
  * d_mean.
- * pixvod_state_size returns the byte count. save synchronises the stream; load
- * enqueues the copies (the host buffer must outlive them) and restores the
- * frame index. EINVAL on a size, magic or geometry mismatch. */
+ * pixvod_state_size returns the byte count. save and load synchronise the
+ * stream (the library's internal state layout differs from this format and is
+ * converted on the host); load restores the frame index. EINVAL on a size,
+ * magic or geometry mismatch. */
 pixvod_status pixvod_state_size(pixvod_handle* h, size_t* bytes);
 pixvod_status pixvod_save_state(pixvod_handle* h, void* h_buf, size_t bytes);
 pixvod_status pixvod_load_state(pixvod_handle* h, const void* h_buf, size_t bytes);

@@ -28,8 +28,10 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     int pitch;
     size_t elt;          // bytes per state element
-    size_t plane_elems;  // pitch * height
+    size_t plane_elems;  // pitch * height (input planes, checkpoint planes)
     size_t plane_bytes;
+    int tiles_x, tiles_y;
+    size_t state_bytes;  // one tile-major state buffer
     size_t off_state[2];
     size_t off_in[6];    // I_s, I_t, g_x, g_y, m_x, m_y
     size_t off_stage_frame, off_stage_normals, off_partials, off_scalars;
@@ -63,10 +65,13 @@ Layout make_layout(const pixvod_intrinsics* K, const pixvod_params* p) {
     L.pitch = (int)align_up((size_t)K->width, kPitchAlign);
     L.plane_elems = (size_t)L.pitch * K->height;
     L.plane_bytes = align_up(L.plane_elems * L.elt, kAlign);
+    L.tiles_x = (K->width + pv::TILE_W - 1) / pv::TILE_W;
+    L.tiles_y = (K->height + pv::TILE_H - 1) / pv::TILE_H;
+    L.state_bytes = align_up((size_t)L.tiles_x * L.tiles_y * pv::TILE_WORDS * L.elt, kAlign);
     size_t off = 0;
     for (int b = 0; b < 2; ++b) {
         L.off_state[b] = off;
-        off += L.plane_bytes * pv::N_PLANES;
+        off += L.state_bytes;
     }
     for (int k = 0; k < 6; ++k) {
         L.off_in[k] = off;
@@ -78,7 +83,7 @@ Layout make_layout(const pixvod_intrinsics* K, const pixvod_params* p) {
     L.off_stage_normals = off;
     off += align_up(npx * 3 * sizeof(float), kAlign);
     L.off_partials = off;
-    off += align_up((size_t)K->height * 7 * sizeof(double), kAlign);  // one partial per row
+    off += align_up((size_t)L.tiles_x * L.tiles_y * 7 * sizeof(double), kAlign);  // one partial per tile
     L.off_scalars = off;
     off += align_up(sizeof(Scalars), kAlign);
     L.total = off;
@@ -115,6 +120,7 @@ Geometry<T> geometry(const pixvod_handle* h) {
     g.H = h->K.height;
     g.pitch = h->L.pitch;
     g.plane = h->L.plane_bytes / sizeof(T);
+    g.tiles_x = h->L.tiles_x;
     g.fx = T(h->K.fx);
     g.fy = T(h->K.fy);
     g.cx = T(h->K.cx);
@@ -155,9 +161,7 @@ dim3 pixel_grid(const pixvod_handle* h) {
     return dim3((h->K.width + 31) / 32, (h->K.height + 3) / 4);
 }
 dim3 sweep_block() { return dim3(pv::SWEEP_BX, pv::SWEEP_BY); }
-dim3 sweep_grid(const pixvod_handle* h) {
-    return dim3((h->K.width + pv::SWEEP_BX - 1) / pv::SWEEP_BX, (h->K.height + pv::SWEEP_BY - 1) / pv::SWEEP_BY);
-}
+dim3 sweep_grid(const pixvod_handle* h) { return dim3(h->L.tiles_x, h->L.tiles_y); }
 
 // dynamic shared memory of the sweep kernel (above the 48 KB default for double)
 template <typename T>
@@ -227,7 +231,7 @@ pixvod_status run_sweeps(pixvod_handle* h, int n) {
 
 template <typename T>
 pixvod_status run_reduce(pixvod_handle* h, int anchor) {
-    pv::k_reduce<T><<<h->K.height, pv::RED_THREADS, 0, h->stream>>>(
+    pv::k_reduce<T><<<h->L.tiles_x * h->L.tiles_y, pv::RED_THREADS, 0, h->stream>>>(
         geometry<T>(h), state_ptr<T>(h, h->cur), reinterpret_cast<double*>(h->ws + h->L.off_partials),
         scalars(h), anchor);
     return launched(h);
@@ -281,10 +285,27 @@ size_t state_blob_bytes(const pixvod_handle* h) {
     return kHeaderBytes + h->L.plane_elems * h->L.elt * kBlobPlanes + kScalarDoubles * sizeof(double);
 }
 
-// device address of blob plane p (state planes, then the input planes)
-char* blob_plane(pixvod_handle* h, int p) {
-    if (p < pv::N_PLANES) return h->ws + h->L.off_state[h->cur] + (size_t)p * h->L.plane_bytes;
-    return h->ws + h->L.off_in[p - pv::N_PLANES];
+// Checkpoint planes are row-major (height x pitch); the state is tile-major.
+// tile_to_rows / rows_to_tile convert one precision's elements on the host.
+template <typename T>
+void tile_to_rows(const pixvod_handle* h, const T* tiles, T* rows) {
+    const size_t pe = h->L.plane_elems;
+    for (int v = 0; v < h->K.height; ++v)
+        for (int u = 0; u < h->K.width; ++u) {
+            const T* src = tiles + pv::state_index(u, v, h->L.tiles_x);
+            T* dst = rows + (size_t)v * h->L.pitch + u;
+            for (int p = 0; p < pv::N_PLANES; ++p) dst[p * pe] = src[p * pv::TILE_PX];
+        }
+}
+template <typename T>
+void rows_to_tile(const pixvod_handle* h, const T* rows, T* tiles) {
+    const size_t pe = h->L.plane_elems;
+    for (int v = 0; v < h->K.height; ++v)
+        for (int u = 0; u < h->K.width; ++u) {
+            T* dst = tiles + pv::state_index(u, v, h->L.tiles_x);
+            const T* src = rows + (size_t)v * h->L.pitch + u;
+            for (int p = 0; p < pv::N_PLANES; ++p) dst[p * pv::TILE_PX] = src[p * pe];
+        }
 }
 
 }  // namespace
@@ -490,11 +511,20 @@ pixvod_status pixvod_save_state(pixvod_handle* h, void* h_buf, size_t bytes) {
     hd[9] = kHeaderBytes + (int64_t)(pb * kBlobPlanes);
     hd[10] = pv::N_INPUT_PLANES;
     hd[11] = h->has_target ? 1 : 0;
-    for (int p = 0; p < kBlobPlanes; ++p) {
-        pixvod_status s = cuda_status(
-            cudaMemcpyAsync(buf + kHeaderBytes + p * pb, blob_plane(h, p), pb, cudaMemcpyDeviceToHost, h->stream));
-        if (s != PIXVOD_OK) return s;
+    std::vector<char> tiles(h->L.state_bytes);
+    pixvod_status s0 = cuda_status(cudaMemcpyAsync(tiles.data(), h->ws + h->L.off_state[h->cur],
+                                                   h->L.state_bytes, cudaMemcpyDeviceToHost, h->stream));
+    if (s0 != PIXVOD_OK) return s0;
+    for (int p = 0; p < pv::N_INPUT_PLANES; ++p) {
+        s0 = cuda_status(cudaMemcpyAsync(buf + kHeaderBytes + (pv::N_PLANES + p) * pb, h->ws + h->L.off_in[p], pb,
+                                         cudaMemcpyDeviceToHost, h->stream));
+        if (s0 != PIXVOD_OK) return s0;
     }
+    if ((s0 = cuda_status(cudaStreamSynchronize(h->stream))) != PIXVOD_OK) return s0;
+    if (h->p.precision == 64)
+        tile_to_rows(h, reinterpret_cast<const double*>(tiles.data()), reinterpret_cast<double*>(buf + kHeaderBytes));
+    else
+        tile_to_rows(h, reinterpret_cast<const float*>(tiles.data()), reinterpret_cast<float*>(buf + kHeaderBytes));
     pixvod_status s = cuda_status(cudaMemcpyAsync(buf + hd[9], scalars(h), kScalarDoubles * sizeof(double),
                                                   cudaMemcpyDeviceToHost, h->stream));
     if (s != PIXVOD_OK) return s;
@@ -511,14 +541,23 @@ pixvod_status pixvod_load_state(pixvod_handle* h, const void* h_buf, size_t byte
         hd[8] != kHeaderBytes || hd[9] != kHeaderBytes + (int64_t)(pb * kBlobPlanes) ||
         hd[10] != pv::N_INPUT_PLANES || (hd[11] != 0 && hd[11] != 1))
         return PIXVOD_EINVAL;
-    for (int p = 0; p < kBlobPlanes; ++p) {
-        pixvod_status s = cuda_status(
-            cudaMemcpyAsync(blob_plane(h, p), buf + kHeaderBytes + p * pb, pb, cudaMemcpyHostToDevice, h->stream));
-        if (s != PIXVOD_OK) return s;
+    std::vector<char> tiles(h->L.state_bytes, 0);
+    if (h->p.precision == 64)
+        rows_to_tile(h, reinterpret_cast<const double*>(buf + kHeaderBytes), reinterpret_cast<double*>(tiles.data()));
+    else
+        rows_to_tile(h, reinterpret_cast<const float*>(buf + kHeaderBytes), reinterpret_cast<float*>(tiles.data()));
+    pixvod_status s0 = cuda_status(cudaMemcpyAsync(h->ws + h->L.off_state[h->cur], tiles.data(), h->L.state_bytes,
+                                                   cudaMemcpyHostToDevice, h->stream));
+    if (s0 != PIXVOD_OK) return s0;
+    for (int p = 0; p < pv::N_INPUT_PLANES; ++p) {
+        s0 = cuda_status(cudaMemcpyAsync(h->ws + h->L.off_in[p], buf + kHeaderBytes + (pv::N_PLANES + p) * pb, pb,
+                                         cudaMemcpyHostToDevice, h->stream));
+        if (s0 != PIXVOD_OK) return s0;
     }
     pixvod_status s = cuda_status(cudaMemcpyAsync(scalars(h), buf + hd[9], kScalarDoubles * sizeof(double),
                                                   cudaMemcpyHostToDevice, h->stream));
     if (s != PIXVOD_OK) return s;
+    if ((s = cuda_status(cudaStreamSynchronize(h->stream))) != PIXVOD_OK) return s;
     h->frame_index = hd[7];
     h->has_target = hd[11] == 1;
     return PIXVOD_OK;

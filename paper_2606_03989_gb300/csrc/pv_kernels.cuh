@@ -1,7 +1,11 @@
 // PixVOD sweep kernels (templated on the arithmetic type).
 //
-// State: structure-of-arrays planes of height x pitch elements, ping-ponged
-// between two buffers (a sweep reads one, writes every plane of the other).
+// State: structure-of-arrays planes stored tile-major: the image is cut into
+// 32 x 4-pixel tiles and each tile keeps all its planes contiguously
+// (plane p of the tile's pixel `lane` at tile_base + p * 128 + lane), so plane
+// offsets are compile-time constants and a tile's message planes are one
+// contiguous block for a bulk copy. Two buffers are ping-ponged: a sweep reads
+// one and writes every plane of the other. Planes:
 //   0..6     mu (xi_0..xi_5, log-depth d)
 //   7..27    M_p: pose information of the belief without the photometric factor
 //            (pose prior plus the four identity messages), 6x6 packed lower
@@ -34,10 +38,16 @@ constexpr int PL_S = 34;
 constexpr int PL_ID = 35;
 constexpr int ID_STRIDE = 27;
 constexpr int PL_NM = 143;
-constexpr int N_INPUT_PLANES = 6;  // I_s, I_t, g_x, g_y, m_x, m_y
+constexpr int N_INPUT_PLANES = 6;  // I_s, I_t, g_x, g_y, m_x, m_y (row-major, pitched)
+constexpr int MSG_PLANES = PL_NM - PL_ID;  // 108: the identity-message planes 35..142
+constexpr int TILE_W = 32;
+constexpr int TILE_H = 4;
+constexpr int TILE_PX = TILE_W * TILE_H;
+constexpr int TILE_WORDS = N_PLANES * TILE_PX;
 
 constexpr unsigned FLAG_NONPOS_PIVOT = 0x1u;
 constexpr unsigned FLAG_NONFINITE = 0x2u;
+constexpr unsigned FLAG_TIMEOUT = 0x4u;
 
 // Device-resident per-handle scalars (doubles, fixed layout; the checkpoint
 // format copies the first 40).
@@ -54,10 +64,16 @@ struct Scalars {
 
 template <typename T>
 struct Geometry {
-    int W, H, pitch;
-    size_t plane;  // elements per plane
+    int W, H, pitch;   // input planes: row-major with `pitch` elements per row
+    size_t plane;      // elements per input plane
+    int tiles_x;       // state: tiles per tile row
     T fx, fy, cx, cy, ifx, ify;
 };
+
+// element offset of pixel (u, v) in a tile-major state buffer (plane 0)
+__host__ __device__ __forceinline__ size_t state_index(int u, int v, int tiles_x) {
+    return (size_t)((v / TILE_H) * tiles_x + (u / TILE_W)) * TILE_WORDS + (v % TILE_H) * TILE_W + (u % TILE_W);
+}
 
 template <typename T>
 struct Factors {
@@ -142,13 +158,13 @@ __global__ void k_reset(Geometry<T> g, Factors<T> f, T* state, const Scalars* sc
     int u = blockIdx.x * blockDim.x + threadIdx.x;
     int v = blockIdx.y * blockDim.y + threadIdx.y;
     if (u >= g.W || v >= g.H) return;
-    size_t i = (size_t)v * g.pitch + u;
+    T* st = state + state_index(u, v, g.tiles_x);
     T d0 = T(sc->d_prior);
-    for (int p = 0; p < N_PLANES; ++p) state[(size_t)p * g.plane + i] = T(0);
-    state[(size_t)6 * g.plane + i] = d0;
+    for (int p = 0; p < N_PLANES; ++p) st[p * TILE_PX] = T(0);
+    st[6 * TILE_PX] = d0;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) state[(size_t)(PL_MP + pidx(k, k)) * g.plane + i] = f.lam_P;
-    state[(size_t)PL_S * g.plane + i] = f.lam_Z;
+    for (int k = 0; k < 6; ++k) st[(PL_MP + pidx(k, k)) * TILE_PX] = f.lam_P;
+    st[PL_S * TILE_PX] = f.lam_Z;
 }
 
 // ---------------------------------------------------------------------------
@@ -162,40 +178,87 @@ __device__ __forceinline__ T bilinear(const T* __restrict__ img, int pitch, int 
     return (T(1) - ay) * ((T(1) - ax) * a + ax * b) + ay * ((T(1) - ax) * c + ax * d);
 }
 
-// Thread block of the sweep kernel: 32 x SWEEP_BY pixels, one thread per pixel
-// (32 x 4 with at least 3 blocks per SM measured fastest on GB300).
-// Each thread keeps the four damped messages it produces in shared memory until
-// the belief solve has given tau (they are then projected and written), so the
-// direction loop is not unrolled and the register footprint stays moderate.
-constexpr int SWEEP_BX = 32;
-constexpr int SWEEP_BY = 4;
-constexpr int SWEEP_THREADS = SWEEP_BX * SWEEP_BY;
-constexpr int MSG_WORDS = 4 * (ID_STRIDE + 2);  // per thread: 4 x (27 identity + 2 normal)
+// ---------------------------------------------------------------------------
+// bulk (TMA) copies global -> shared with an mbarrier, in inline PTX
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// dst, src and bytes must be multiples of 16 bytes
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// bounded wait for phase `parity`; false if it did not complete
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Thread block of the sweep kernel: one state tile (32 x 4 pixels), one thread
+// per pixel; 4 blocks per SM (55 KB of shared memory and at most 128 registers
+// each). Each thread keeps its four damped identity messages in shared memory
+// until the belief solve has given tau (they are then projected and written), so
+// the direction loop is not unrolled; the normal messages stay in registers.
+constexpr int SWEEP_BX = TILE_W;
+constexpr int SWEEP_BY = TILE_H;
+constexpr int SWEEP_THREADS = TILE_PX;
 
 template <typename T>
 constexpr size_t sweep_smem_bytes() {
-    return sizeof(T) * MSG_WORDS * SWEEP_THREADS;
+    return sizeof(T) * MSG_PLANES * TILE_PX;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* msg = reinterpret_cast<T*>(smem_raw);  // msg[w * SWEEP_THREADS + tid]
+__global__ void __launch_bounds__(SWEEP_THREADS, 4) k_sweep(const SweepArgs<T> a) {
+    // msg[p * TILE_PX + tid]: this tile's 108 identity-message planes, bulk-copied
+    // in at the start (the old messages), overwritten in place by the damped new ones
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    T* msg = reinterpret_cast<T*>(smem_raw);
     const int tid = threadIdx.y * SWEEP_BX + threadIdx.x;
     const int u = blockIdx.x * SWEEP_BX + threadIdx.x;
     const int v = blockIdx.y * SWEEP_BY + threadIdx.y;
     const Geometry<T>& g = a.g;
     const Factors<T>& F = a.f;
+    const size_t tile = (size_t)blockIdx.y * g.tiles_x + blockIdx.x;
+    if (tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+        constexpr unsigned bytes = sizeof(T) * MSG_PLANES * TILE_PX;
+        mbar_expect_tx(&bar, bytes);
+        bulk_copy_g2s(msg, a.in + tile * TILE_WORDS + PL_ID * TILE_PX, bytes, &bar);
+    }
     if (u >= g.W || v >= g.H) return;
-    const int PS = (int)g.plane;
     const int i = v * g.pitch + u;
-    const T* __restrict__ S = a.in;
-    T* __restrict__ D = a.out;
+    const T* __restrict__ Si = a.in + tile * TILE_WORDS + tid;   // this pixel, plane 0
+    T* __restrict__ Di = a.out + tile * TILE_WORDS + tid;
 
     T xi[6], d;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) xi[k] = S[k * PS + i];
-    d = S[6 * PS + i];
+    for (int k = 0; k < 6; ++k) xi[k] = Si[k * TILE_PX];
+    d = Si[6 * TILE_PX];
     T R[9], t[3];
     se3_exp(xi, R, t);
 
@@ -278,28 +341,33 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs<T> a
 
     // --- a2/a3: pairwise messages from the four neighbours ---
     unsigned flags = 0;
+    if (!mbar_wait_bounded(&bar, 0)) {
+        // the tile's messages never arrived: flag it, wait once more, leave the tile
+        atomicOr(&a.sc->flags, FLAG_TIMEOUT);
+        mbar_wait_bounded(&bar, 0);
+        return;
+    }
     const T beta = F.beta, omb = T(1) - F.beta;
+    T nl0 = T(0), ne0 = T(0), nl1 = T(0), ne1 = T(0), nl2 = T(0), ne2 = T(0), nl3 = T(0), ne3 = T(0);
 #pragma unroll 1
     for (int k = 0; k < 4; ++k) {
-        T* mb = msg + (k * (ID_STRIDE + 2)) * SWEEP_THREADS + tid;
+        T* mb = msg + (k * ID_STRIDE) * TILE_PX + tid;          // identity slot k
         const int un = u + (k == 0 ? -1 : (k == 1 ? 1 : 0));
         const int vn = v + (k == 2 ? -1 : (k == 3 ? 1 : 0));
         const bool has = un >= 0 && un < g.W && vn >= 0 && vn < g.H;
         if (!has) {
 #pragma unroll
-            for (int q = 0; q < ID_STRIDE + 2; ++q) mb[q * SWEEP_THREADS] = T(0);
+            for (int q = 0; q < ID_STRIDE; ++q) mb[q * TILE_PX] = T(0);
             continue;
         }
-        const int j = vn * g.pitch + un;
         const int ko = k ^ 1;
-        const T* Sj = S + j;
-        const T* Si = S + i;
+        const T* Sj = a.in + state_index(un, vn, g.tiles_x);
         // identity factor (Eq. 5): r = Log(Exp(xi_j)^-1 Exp(xi_i)), J_i = I, J_j = -I
         T rb[6];
         {
             T xj[6];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) xj[q] = Sj[q * PS];
+            for (int q = 0; q < 6; ++q) xj[q] = Sj[q * TILE_PX];
             T Rj[9], tj[3], Rr[9], tr[3];
             se3_exp(xj, Rj, tj);
             se3_invmul(Rj, tj, R, t, Rr, tr);
@@ -307,22 +375,22 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs<T> a
         }
         // variable-to-factor marginal of j: V = W + u u^T with W = M_p,j - Lambda_{f->j}
         // (pose prior plus j's three other identity messages) and u = u_j
-        const T* mj = Sj + (PL_ID + ID_STRIDE * ko) * PS;
+        const T* mj = Sj + (PL_ID + ID_STRIDE * ko) * TILE_PX;
         T W[21], C[21], uj[6], gv[6];
 #pragma unroll
         for (int q = 0; q < 21; ++q) {
-            W[q] = Sj[(PL_MP + q) * PS] - mj[q * PS];
+            W[q] = Sj[(PL_MP + q) * TILE_PX] - mj[q * TILE_PX];
             C[q] = W[q];
         }
 #pragma unroll
-        for (int q = 0; q < 6; ++q) uj[q] = Sj[(PL_U + q) * PS];
+        for (int q = 0; q < 6; ++q) uj[q] = Sj[(PL_U + q) * TILE_PX];
         // g0 = eta_v - W r with eta_v = -eta_{f->j}
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             T wr = T(0);
 #pragma unroll
             for (int c = 0; c < 6; ++c) wr += W[pidx(q, c)] * rb[c];
-            gv[q] = -mj[(21 + q) * PS] - wr;
+            gv[q] = -mj[(21 + q) * TILE_PX] - wr;
         }
         // A = W + lam_R I is well conditioned (W is bounded by a few lam_R)
 #pragma unroll
@@ -349,12 +417,11 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs<T> a
         const T crank = F.lam_R * F.lam_R * iuz;
         // eta_msg = lam_R C^-1 (eta_v - V r) = lam_R (h - z (u^T r + u^T h) / (1 + u^T z))
         const T ecoef = (ur + uh) * iuz;
-        const T* mi = Si + (PL_ID + ID_STRIDE * k) * PS;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-            T e = omb * (F.lam_R * (gv[q] - ecoef * z[q])) + beta * mi[(21 + q) * PS];
+            T e = omb * (F.lam_R * (gv[q] - ecoef * z[q])) + beta * mb[(21 + q) * TILE_PX];
             eb[q] += e;
-            mb[(21 + q) * SWEEP_THREADS] = e;
+            mb[(21 + q) * TILE_PX] = e;
         }
         // Y = L^-1 W in place of W (columns), then Lambda = W - Y^T Y + crank z z^T
         {
@@ -373,26 +440,28 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs<T> a
 #pragma unroll
                     for (int q = 0; q < 6; ++q) yy += Y[r][q] * Y[c][q];
                     T lnew = W[pidx(r, c)] - yy + crank * z[r] * z[c];
-                    T l = omb * lnew + beta * mi[pidx(r, c) * PS];
+                    T l = omb * lnew + beta * mb[pidx(r, c) * TILE_PX];
                     Mp[pidx(r, c)] += l;
-                    mb[pidx(r, c) * SWEEP_THREADS] = l;
+                    mb[pidx(r, c) * TILE_PX] = l;
                 }
         }
 
         // normal-integration factor (Eq. 6): r_i = d_i - d_j + sg m
-        T dj = Sj[6 * PS];
-        T sv = Sj[PL_S * PS] - Sj[(PL_NM + 2 * ko) * PS];
-        T evn = -Sj[(PL_NM + 2 * ko + 1) * PS];
+        T dj = Sj[6 * TILE_PX];
+        T sv = Sj[PL_S * TILE_PX] - Sj[(PL_NM + 2 * ko) * TILE_PX];
+        T evn = -Sj[(PL_NM + 2 * ko + 1) * TILE_PX];
         T m = k == 0 ? a.m_x[i - 1] : (k == 1 ? a.m_x[i] : (k == 2 ? a.m_y[i - g.pitch] : a.m_y[i]));
         T sg = (k == 0 || k == 2) ? T(1) : T(-1);
         T rn = d - dj + sg * m;
         T den = v_div(T(1), F.lam_N + sv);
-        T nnew = omb * (F.lam_N * sv * den) + beta * Si[(PL_NM + 2 * k) * PS];
-        T enew = omb * (F.lam_N * (evn - sv * rn) * den) + beta * Si[(PL_NM + 2 * k + 1) * PS];
+        T nnew = omb * (F.lam_N * sv * den) + beta * Si[(PL_NM + 2 * k) * TILE_PX];
+        T enew = omb * (F.lam_N * (evn - sv * rn) * den) + beta * Si[(PL_NM + 2 * k + 1) * TILE_PX];
         md += nnew;
         eb[6] += enew;
-        mb[ID_STRIDE * SWEEP_THREADS] = nnew;
-        mb[(ID_STRIDE + 1) * SWEEP_THREADS] = enew;
+        if (k == 0) { nl0 = nnew; ne0 = enew; }
+        else if (k == 1) { nl1 = nnew; ne1 = enew; }
+        else if (k == 2) { nl2 = nnew; ne2 = enew; }
+        else { nl3 = nnew; ne3 = enew; }
     }
 
     // --- a4: belief, mean update, tangent projection ---
@@ -444,7 +513,6 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs<T> a
 #pragma unroll
         for (int q = 0; q < 7; ++q) tau[q] = T(0);
     }
-    T* Di = D + i;
     // mu <- mu (+) tau
     {
         T Rt[9], tt[3], Rn[9], tn[3], xn[6];
@@ -452,39 +520,44 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs<T> a
         se3_mul(R, t, Rt, tt, Rn, tn);
         se3_log(Rn, tn, xn);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) Di[q * PS] = xn[q];
-        Di[6 * PS] = d + tau[6];
+        for (int q = 0; q < 6; ++q) Di[q * TILE_PX] = xn[q];
+        Di[6 * TILE_PX] = d + tau[6];
     }
     {
         const T bp = v_div(alpha * md, md + alpha * J[6] * J[6]);
         const T sb = v_sqrt(bp);
 #pragma unroll
-        for (int q = 0; q < 21; ++q) Di[(PL_MP + q) * PS] = Mp[q];
+        for (int q = 0; q < 21; ++q) Di[(PL_MP + q) * TILE_PX] = Mp[q];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) Di[(PL_U + q) * PS] = sb * J[q];
-        Di[PL_S * PS] = md + v_div(alpha * J[6] * J[6], T(1) + alpha * qv);
+        for (int q = 0; q < 6; ++q) Di[(PL_U + q) * TILE_PX] = sb * J[q];
+        Di[PL_S * TILE_PX] = md + v_div(alpha * J[6] * J[6], T(1) + alpha * qv);
     }
     // messages, projected: eta <- eta - Lambda tau
+    Di[(PL_NM + 0) * TILE_PX] = nl0;
+    Di[(PL_NM + 1) * TILE_PX] = ne0 - nl0 * tau[6];
+    Di[(PL_NM + 2) * TILE_PX] = nl1;
+    Di[(PL_NM + 3) * TILE_PX] = ne1 - nl1 * tau[6];
+    Di[(PL_NM + 4) * TILE_PX] = nl2;
+    Di[(PL_NM + 5) * TILE_PX] = ne2 - nl2 * tau[6];
+    Di[(PL_NM + 6) * TILE_PX] = nl3;
+    Di[(PL_NM + 7) * TILE_PX] = ne3 - nl3 * tau[6];
 #pragma unroll 1
     for (int k = 0; k < 4; ++k) {
-        const T* mb = msg + (k * (ID_STRIDE + 2)) * SWEEP_THREADS + tid;
-        T* dk = Di + (PL_ID + ID_STRIDE * k) * PS;
+        const T* mb = msg + (k * ID_STRIDE) * TILE_PX + tid;
+        T* dk = Di + (PL_ID + ID_STRIDE * k) * TILE_PX;
         T L[21];
 #pragma unroll
         for (int q = 0; q < 21; ++q) {
-            L[q] = mb[q * SWEEP_THREADS];
-            dk[q * PS] = L[q];
+            L[q] = mb[q * TILE_PX];
+            dk[q * TILE_PX] = L[q];
         }
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
-            T e = mb[(21 + r) * SWEEP_THREADS];
+            T e = mb[(21 + r) * TILE_PX];
 #pragma unroll
             for (int c = 0; c < 6; ++c) e -= L[pidx(r, c)] * tau[c];
-            dk[(21 + r) * PS] = e;
+            dk[(21 + r) * TILE_PX] = e;
         }
-        T n = mb[ID_STRIDE * SWEEP_THREADS];
-        Di[(PL_NM + 2 * k) * PS] = n;
-        Di[(PL_NM + 2 * k + 1) * PS] = mb[(ID_STRIDE + 1) * SWEEP_THREADS] - n * tau[6];
     }
     if (flags) atomicOr(&a.sc->flags, flags);
 }
@@ -492,10 +565,10 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 3) k_sweep(const SweepArgs<T> a
 // ---------------------------------------------------------------------------
 // a5: pose average (App. C.2) and keyframe anchoring, one launch, fixed order
 // ---------------------------------------------------------------------------
-constexpr int RED_THREADS = 256;
+constexpr int RED_THREADS = TILE_PX;
 
-// One block per image row sums that row's 7 mean planes (double accumulation,
-// fixed order); the last block to finish sums the row partials in row order,
+// One block per state tile sums that tile's 7 mean planes (double accumulation,
+// fixed order); the last block to finish sums the tile partials in tile order,
 // writes xi_est and the mean log-depth, composes T_cur = Exp(xi_est) T_kf and,
 // at an anchoring frame, moves the keyframe: T_kf <- T_cur, d_prior <- d_mean.
 template <typename T>
@@ -505,12 +578,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(Geometry<T> g, const T* 
     __shared__ double sh[7][RED_THREADS];
     __shared__ bool last;
     const int tid = threadIdx.x;
-    const int row = blockIdx.x;
+    const int tile = blockIdx.x;
+    const int u = (tile % g.tiles_x) * TILE_W + tid % TILE_W;
+    const int v = (tile / g.tiles_x) * TILE_H + tid / TILE_W;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    const T* base = state + (size_t)row * g.pitch;
-    for (int u = tid; u < g.W; u += RED_THREADS)
+    if (tid < TILE_PX && u < g.W && v < g.H) {
+        const T* st = state + (size_t)tile * TILE_WORDS + tid;
 #pragma unroll
-        for (int q = 0; q < 7; ++q) acc[q] += double(base[q * g.plane + u]);
+        for (int q = 0; q < 7; ++q) acc[q] = double(st[q * TILE_PX]);
+    }
 #pragma unroll
     for (int q = 0; q < 7; ++q) sh[q][tid] = acc[q];
     __syncthreads();
@@ -522,7 +598,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(Geometry<T> g, const T* 
     }
     if (tid == 0) {
 #pragma unroll
-        for (int q = 0; q < 7; ++q) partials[row * 7 + q] = sh[q][0];
+        for (int q = 0; q < 7; ++q) partials[tile * 7 + q] = sh[q][0];
         __threadfence();
         last = atomicAdd(&sc->counter, 1u) == (unsigned)(gridDim.x - 1);
     }
@@ -573,7 +649,7 @@ __global__ void k_depth_out(Geometry<T> g, const T* __restrict__ state, float* o
     int u = blockIdx.x * blockDim.x + threadIdx.x;
     int v = blockIdx.y * blockDim.y + threadIdx.y;
     if (u >= g.W || v >= g.H) return;
-    out[(size_t)v * g.W + u] = float(v_exp(sign * state[6 * g.plane + (size_t)v * g.pitch + u]));
+    out[(size_t)v * g.W + u] = float(v_exp(sign * state[state_index(u, v, g.tiles_x) + 6 * TILE_PX]));
 }
 
 }  // namespace pv
