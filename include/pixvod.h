@@ -205,6 +205,77 @@ pixvod_status pixvod_get_profile(pixvod_handle* h, pixvod_profile* out);
 /* Number of kernels this handle has launched since creation. */
 pixvod_status pixvod_launch_count(pixvod_handle* h, int64_t* out);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent sequences (each with its own intrinsics, image size
+ * and state, all with the same params) advanced together, one frame per call.
+ * Each sequence's results are bit-identical to tracking it alone with
+ * pixvod_track; only the scheduling of the work differs:
+ *   PIXVOD_SCHED_PLAIN       every sequence runs its own launches in turn;
+ *   PIXVOD_SCHED_BATCHED     one launch per sweep covers the tiles of all
+ *                            sequences;
+ *   PIXVOD_SCHED_PERSISTENT  one cooperative launch per frame runs all sweeps of
+ *                            all sequences, blocks meeting at a bounded grid
+ *                            barrier between sweeps (blocks_per_sm resident
+ *                            blocks per SM, 1..4).
+ * The keyframe count rule applies to the batch's frame index.
+ * --------------------------------------------------------------------------- */
+typedef struct pixvod_batch pixvod_batch;
+
+#define PIXVOD_SCHED_PLAIN 0
+#define PIXVOD_SCHED_BATCHED 1
+#define PIXVOD_SCHED_PERSISTENT 2
+
+/* Device workspace bytes for n sequences with intrinsics K[0..n-1]. No CUDA calls. */
+pixvod_status pixvod_batch_workspace_bytes(int32_t n, const pixvod_intrinsics* K, const pixvod_params* p,
+                                           size_t* out_bytes);
+
+/* Create a batch on a caller-owned 256-byte aligned workspace (as pixvod_create).
+ * The schedule starts as PIXVOD_SCHED_PERSISTENT with 4 blocks per SM.
+ * Synchronises the stream. EINVAL / ENOMEM as pixvod_create; n >= 1. */
+pixvod_status pixvod_batch_create(int32_t n, const pixvod_intrinsics* K, const pixvod_params* p, void* d_workspace,
+                                  size_t ws_bytes, void* stream, pixvod_batch** out);
+pixvod_status pixvod_batch_destroy(pixvod_batch* b);
+
+/* Register the input buffers: d_frames[i] (width_i*height_i float32) and
+ * d_normals[i] (width_i*height_i*3 float32, read at keyframes) are device
+ * pointers, arrays of n host entries. Every pixvod_batch_track call reads them
+ * (so a captured CUDA graph of pixvod_batch_track can be replayed after the
+ * caller writes new frames into the same buffers). May be called again to point
+ * at other buffers. EINVAL on a null or misaligned pointer. */
+pixvod_status pixvod_batch_set_inputs(pixvod_batch* b, const float* const* d_frames, const float* const* d_normals);
+
+/* Advance every sequence by one frame from the registered buffers (semantics of
+ * pixvod_track). Asynchronous; ESTATE before pixvod_batch_set_inputs. */
+pixvod_status pixvod_batch_track(pixvod_batch* b, int32_t n_iters);
+
+/* xi_est of every sequence, 6 doubles per sequence into host memory. Synchronises. */
+pixvod_status pixvod_batch_get_poses(pixvod_batch* b, double* xi);
+
+/* OR of every sequence's device flags and the batch's own. Synchronises; ENUMERIC
+ * when any flag is set. */
+pixvod_status pixvod_batch_get_status(pixvod_batch* b, uint32_t* flags);
+
+/* Checkpoint of sequence i, in the pixvod_save_state format. Synchronises. */
+pixvod_status pixvod_batch_state_size(pixvod_batch* b, int32_t i, size_t* bytes);
+pixvod_status pixvod_batch_save_state(pixvod_batch* b, int32_t i, void* h_buf, size_t bytes);
+
+/* Choose the schedule (and blocks per SM for the persistent one, 1..4, clamped
+ * to what the device can hold resident). EINVAL on an unknown schedule. */
+pixvod_status pixvod_batch_set_schedule(pixvod_batch* b, int32_t schedule, int32_t blocks_per_sm);
+pixvod_status pixvod_batch_get_schedule(pixvod_batch* b, int32_t* schedule, int32_t* blocks_per_sm);
+
+/* Autotuner: times every schedule (plain, batched, persistent with 2, 3 and 4
+ * blocks per SM) on `reps` runs of n_iters sweeps, each sequence tracking its
+ * keyframe against itself, keeps the fastest, and restores every sequence's
+ * keyframe state. Valid right after the first pixvod_batch_track (frame index 1)
+ * while the registered frame buffers still hold the keyframes (ESTATE
+ * otherwise). Synchronises. times_ms (optional, 5 entries) receives the mean
+ * time per run of each candidate in that order. */
+pixvod_status pixvod_batch_autotune(pixvod_batch* b, int32_t n_iters, int32_t reps, float* times_ms);
+
+/* Kernels the batch has launched since creation. */
+pixvod_status pixvod_batch_launch_count(pixvod_batch* b, int64_t* out);
+
 /* Pose average without any device allocation. The paper has no counterpart: this
  * is a library convenience for callers that cannot allocate device memory, such
  * as code that runs while a CUDA stream is being captured, a real-time loop that

@@ -9,16 +9,17 @@ without the library.
 import importlib
 
 _NATIVE = {"ECUDA", "EINVAL", "ENOMEM", "ENUMERIC", "ESTATE", "ETIMEOUT", "FLAG_NONFINITE",
+           "SCHED_PLAIN", "SCHED_BATCHED", "SCHED_PERSISTENT", "SCHED_NAMES",
            "FLAG_NONPOS_PIVOT", "FLAG_TIMEOUT", "LIB_PATH", "OK", "PixvodError", "StateView",
            "intrinsics", "lib", "params", "params_default", "parse_state", "status_string",
            "workspace_bytes"}
 
-__all__ = sorted(_NATIVE | {"Tracker"})
+__all__ = sorted(_NATIVE | {"Tracker", "Batch"})
 
 
 def __getattr__(name):
     if name in _NATIVE:
         return getattr(importlib.import_module("._native", __name__), name)
-    if name == "Tracker":
-        return importlib.import_module(".tracker", __name__).Tracker
+    if name in ("Tracker", "Batch"):
+        return getattr(importlib.import_module(".tracker", __name__), name)
     raise AttributeError(name)

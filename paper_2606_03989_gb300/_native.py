@@ -16,6 +16,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "lib", "libpixvod.so")
 
 OK, EINVAL, ECUDA, ENUMERIC, ESTATE, ETIMEOUT, ENOMEM = range(7)
+SCHED_PLAIN, SCHED_BATCHED, SCHED_PERSISTENT = 0, 1, 2
+SCHED_NAMES = {SCHED_PLAIN: "plain", SCHED_BATCHED: "batched", SCHED_PERSISTENT: "persistent"}
 FLAG_NONPOS_PIVOT, FLAG_NONFINITE, FLAG_TIMEOUT = 0x1, 0x2, 0x4
 N_PLANES = 151
 N_INPUT_PLANES = 6
@@ -78,6 +80,20 @@ def _load():
         "pixvod_get_profile": (S, [H, ctypes.POINTER(pixvod_profile)]),
         "pixvod_launch_count": (S, [H, ctypes.POINTER(I64)]),
         "pixvod_pose_mean_static": (S, [P, I32, I32, I64, I64, P, P]),
+        "pixvod_batch_workspace_bytes": (S, [I32, P, ctypes.POINTER(pixvod_params), ctypes.POINTER(ctypes.c_size_t)]),
+        "pixvod_batch_create": (S, [I32, P, ctypes.POINTER(pixvod_params), P, ctypes.c_size_t, P,
+                                    ctypes.POINTER(H)]),
+        "pixvod_batch_destroy": (S, [H]),
+        "pixvod_batch_set_inputs": (S, [H, P, P]),
+        "pixvod_batch_track": (S, [H, I32]),
+        "pixvod_batch_get_poses": (S, [H, P]),
+        "pixvod_batch_get_status": (S, [H, ctypes.POINTER(ctypes.c_uint32)]),
+        "pixvod_batch_state_size": (S, [H, I32, ctypes.POINTER(ctypes.c_size_t)]),
+        "pixvod_batch_save_state": (S, [H, I32, P, ctypes.c_size_t]),
+        "pixvod_batch_set_schedule": (S, [H, I32, I32]),
+        "pixvod_batch_get_schedule": (S, [H, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "pixvod_batch_autotune": (S, [H, I32, I32, P]),
+        "pixvod_batch_launch_count": (S, [H, ctypes.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -11,7 +11,7 @@
 #include <vector>
 
 #include "../../include/pixvod.h"
-#include "pv_kernels.cuh"
+#include "pv_batch.cuh"
 
 using pv::Factors;
 using pv::Geometry;
@@ -22,6 +22,8 @@ namespace {
 constexpr int kPitchAlign = 32;       // elements per row rounded up to 32
 constexpr size_t kAlign = 256;        // every workspace region starts on 256 bytes
 constexpr int kProfilePairs = 4096;
+constexpr size_t kDescBytes = 512;    // room for one SeqDesc<float> or SeqDesc<double>
+static_assert(sizeof(pv::SeqDesc<double>) <= kDescBytes, "descriptor size");
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -35,6 +37,7 @@ struct Layout {
     size_t off_state[2];
     size_t off_in[6];    // I_s, I_t, g_x, g_y, m_x, m_y
     size_t off_stage_frame, off_stage_normals, off_partials, off_scalars;
+    size_t off_desc;     // the sweep kernel's descriptor of this sequence
     size_t total;
 };
 
@@ -86,6 +89,8 @@ Layout make_layout(const pixvod_intrinsics* K, const pixvod_params* p) {
     off += align_up((size_t)L.tiles_x * L.tiles_y * 7 * sizeof(double), kAlign);  // one partial per tile
     L.off_scalars = off;
     off += align_up(sizeof(Scalars), kAlign);
+    L.off_desc = off;
+    off += kDescBytes;
     L.total = off;
     return L;
 }
@@ -156,17 +161,37 @@ T* input_ptr(pixvod_handle* h, int k) {
 }
 Scalars* scalars(pixvod_handle* h) { return reinterpret_cast<Scalars*>(h->ws + h->L.off_scalars); }
 
+template <typename T>
+pv::SeqDesc<T> seq_desc(pixvod_handle* h, const float* frame, const float* normals) {
+    pv::SeqDesc<T> d;
+    d.g = geometry<T>(h);
+    d.f = factors<T>(h);
+    d.state[0] = state_ptr<T>(h, 0);
+    d.state[1] = state_ptr<T>(h, 1);
+    for (int k = 0; k < pv::N_INPUT_PLANES; ++k) d.in_planes[k] = input_ptr<T>(h, k);
+    d.sc = scalars(h);
+    d.partials = reinterpret_cast<double*>(h->ws + h->L.off_partials);
+    d.frame = frame;
+    d.normals = normals;
+    d.n_tiles = h->L.tiles_x * h->L.tiles_y;
+    return d;
+}
+
+template <typename T>
+const pv::SeqDesc<T>* desc_ptr(pixvod_handle* h) {
+    return reinterpret_cast<const pv::SeqDesc<T>*>(h->ws + h->L.off_desc);
+}
+
 dim3 pixel_block() { return dim3(32, 4); }
 dim3 pixel_grid(const pixvod_handle* h) {
     return dim3((h->K.width + 31) / 32, (h->K.height + 3) / 4);
 }
 dim3 sweep_block() { return dim3(pv::SWEEP_BX, pv::SWEEP_BY); }
-dim3 sweep_grid(const pixvod_handle* h) { return dim3(h->L.tiles_x, h->L.tiles_y); }
 
 // dynamic shared memory of the sweep kernel (above the 48 KB default for double)
 template <typename T>
 cudaError_t sweep_attributes() {
-    static cudaError_t once = cudaFuncSetAttribute(pv::k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    static cudaError_t once = cudaFuncSetAttribute(pv::k_sweeps<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)pv::sweep_smem_bytes<T>());
     return once;
 }
@@ -175,6 +200,17 @@ pixvod_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return PIXVOD_OK;
     fprintf(stderr, "pixvod: CUDA error %s\n", cudaGetErrorString(e));
     return PIXVOD_ECUDA;
+}
+
+// the handle's sweep descriptor (pointers into its workspace, geometry, factor
+// weights); written once, the stream is synchronised before the host copy dies
+pixvod_status upload_desc(pixvod_handle* h) {
+    if (h->p.precision == 64) {
+        pv::SeqDesc<double> d = seq_desc<double>(h, nullptr, nullptr);
+        return cuda_status(cudaMemcpyAsync(h->ws + h->L.off_desc, &d, sizeof(d), cudaMemcpyHostToDevice, h->stream));
+    }
+    pv::SeqDesc<float> d = seq_desc<float>(h, nullptr, nullptr);
+    return cuda_status(cudaMemcpyAsync(h->ws + h->L.off_desc, &d, sizeof(d), cudaMemcpyHostToDevice, h->stream));
 }
 
 pixvod_status launched(pixvod_handle* h) {
@@ -199,25 +235,15 @@ template <typename T>
 pixvod_status run_sweeps(pixvod_handle* h, int n) {
     pixvod_status st = cuda_status(sweep_attributes<T>());
     if (st != PIXVOD_OK) return st;
-    pv::SweepArgs<T> a;
-    a.g = geometry<T>(h);
-    a.f = factors<T>(h);
-    a.I_s = input_ptr<T>(h, 0);
-    a.I_t = input_ptr<T>(h, 1);
-    a.g_x = input_ptr<T>(h, 2);
-    a.g_y = input_ptr<T>(h, 3);
-    a.m_x = input_ptr<T>(h, 4);
-    a.m_y = input_ptr<T>(h, 5);
-    a.sc = scalars(h);
+    const int n_tiles = h->L.tiles_x * h->L.tiles_y;
     for (int it = 0; it < n; ++it) {
-        a.in = state_ptr<T>(h, h->cur);
-        a.out = state_ptr<T>(h, h->cur ^ 1);
         bool prof = h->profiling;
         if (prof) {
             if (h->ev_used == kProfilePairs) harvest_profile(h);
             cudaEventRecord(h->ev[2 * h->ev_used], h->stream);
         }
-        pv::k_sweep<T><<<sweep_grid(h), sweep_block(), pv::sweep_smem_bytes<T>(), h->stream>>>(a);
+        pv::k_sweeps<T><<<n_tiles, sweep_block(), pv::sweep_smem_bytes<T>(), h->stream>>>(
+            desc_ptr<T>(h), nullptr, n_tiles, 1, h->cur, pv::GridSync{nullptr, nullptr, nullptr});
         pixvod_status s = launched(h);
         if (prof) {
             cudaEventRecord(h->ev[2 * h->ev_used + 1], h->stream);
@@ -384,6 +410,7 @@ pixvod_status pixvod_create(const pixvod_intrinsics* K, const pixvod_params* p, 
         s = cuda_status(cudaMemcpyAsync(sc->T_kf, eye, sizeof(eye), cudaMemcpyHostToDevice, h->stream));
         if (s == PIXVOD_OK)
             s = cuda_status(cudaMemcpyAsync(sc->T_cur, eye, sizeof(eye), cudaMemcpyHostToDevice, h->stream));
+        if (s == PIXVOD_OK) s = upload_desc(h);
         if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(h->stream));
     }
     if (s != PIXVOD_OK) {
@@ -594,6 +621,421 @@ pixvod_status pixvod_get_profile(pixvod_handle* h, pixvod_profile* out) {
 pixvod_status pixvod_launch_count(pixvod_handle* h, int64_t* out) {
     if (!h || !out) return PIXVOD_EINVAL;
     *out = h->launches;
+    return PIXVOD_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// batches
+// ===========================================================================
+struct pixvod_batch {
+    int n;
+    pixvod_params p;
+    cudaStream_t stream;
+    std::vector<pixvod_handle> seq;
+    char* ws;
+    size_t off_desc, off_work, off_sync;
+    int n_work;
+    int schedule;
+    int blocks_per_sm;
+    int max_blocks_per_sm;
+    int num_sms;
+    bool inputs_set;
+    std::vector<const float*> frames, normals;
+    int64_t frame_index;
+    int64_t launches;
+};
+
+namespace {
+
+struct BatchLayout {
+    std::vector<Layout> seq;
+    std::vector<size_t> off_seq;
+    size_t off_desc, off_work, off_sync, total;
+    int n_work;
+};
+
+BatchLayout make_batch_layout(int n, const pixvod_intrinsics* K, const pixvod_params* p) {
+    BatchLayout B;
+    size_t off = 0;
+    B.n_work = 0;
+    for (int i = 0; i < n; ++i) {
+        B.seq.push_back(make_layout(&K[i], p));
+        B.off_seq.push_back(off);
+        off += align_up(B.seq.back().total, kAlign);
+        B.n_work += B.seq.back().tiles_x * B.seq.back().tiles_y;
+    }
+    B.off_desc = off;
+    off += align_up((size_t)n * kDescBytes, kAlign);
+    B.off_work = off;
+    off += align_up((size_t)B.n_work * sizeof(pv::Work), kAlign);
+    B.off_sync = off;
+    off += kAlign;
+    B.total = off;
+    return B;
+}
+
+
+// descriptors are an array of SeqDesc<T> (the kernels index it with that stride)
+template <typename T>
+pixvod_status upload_descs(pixvod_batch* b) {
+    std::vector<pv::SeqDesc<T>> host(b->n);
+    for (int i = 0; i < b->n; ++i) host[i] = seq_desc<T>(&b->seq[i], b->frames[i], b->normals[i]);
+    // pageable source: the copy is staged before the call returns
+    return cuda_status(cudaMemcpyAsync(b->ws + b->off_desc, host.data(), host.size() * sizeof(pv::SeqDesc<T>),
+                                       cudaMemcpyHostToDevice, b->stream));
+}
+
+template <typename T>
+const pv::SeqDesc<T>* descs(pixvod_batch* b) {
+    return reinterpret_cast<const pv::SeqDesc<T>*>(b->ws + b->off_desc);
+}
+const pv::Work* works(pixvod_batch* b) { return reinterpret_cast<const pv::Work*>(b->ws + b->off_work); }
+unsigned* batch_sync(pixvod_batch* b) { return reinterpret_cast<unsigned*>(b->ws + b->off_sync); }
+
+pixvod_status batch_launched(pixvod_batch* b) {
+    b->launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+
+// sweeps of all sequences under the batch's (non-plain) schedule; every
+// sequence's `cur` advances together
+template <typename T>
+pixvod_status batch_sweeps(pixvod_batch* b, int n_iters, int schedule) {
+    if (n_iters <= 0) return PIXVOD_OK;
+    pixvod_status s = cuda_status(sweep_attributes<T>());
+    if (s != PIXVOD_OK) return s;
+    int cur = b->seq[0].cur;
+    if (schedule == PIXVOD_SCHED_BATCHED) {
+        for (int it = 0; it < n_iters; ++it) {
+            pv::k_sweeps<T><<<b->n_work, sweep_block(), pv::sweep_smem_bytes<T>(), b->stream>>>(
+                descs<T>(b), works(b), b->n_work, 1, cur, pv::GridSync{nullptr, nullptr, nullptr});
+            if ((s = batch_launched(b)) != PIXVOD_OK) return s;
+            cur ^= 1;
+        }
+    } else {
+        unsigned* sy = batch_sync(b);
+        if ((s = cuda_status(cudaMemsetAsync(sy, 0, sizeof(unsigned), b->stream))) != PIXVOD_OK) return s;
+        pv::GridSync gs{sy, sy + 1, sy + 2};
+        int grid = b->blocks_per_sm * b->num_sms;
+        if (grid > b->n_work) grid = b->n_work;
+        const pv::SeqDesc<T>* d = descs<T>(b);
+        const pv::Work* w = works(b);
+        int n_work = b->n_work, cur0 = cur;
+        void* args[] = {(void*)&d, (void*)&w, (void*)&n_work, (void*)&n_iters, (void*)&cur0, (void*)&gs};
+        s = cuda_status(cudaLaunchCooperativeKernel((const void*)pv::k_sweeps<T>, dim3(grid), sweep_block(),
+                                                    args, pv::sweep_smem_bytes<T>(), b->stream));
+        b->launches++;
+        if (s != PIXVOD_OK) return s;
+        cur ^= (n_iters & 1);
+    }
+    for (auto& h : b->seq) h.cur = cur;
+    return PIXVOD_OK;
+}
+
+template <typename T>
+pixvod_status batch_keyframe(pixvod_batch* b) {
+    pv::k_batch_keyframe<T><<<b->n_work, pixel_block(), 0, b->stream>>>(descs<T>(b), works(b), b->seq[0].cur);
+    return batch_launched(b);
+}
+
+template <typename T>
+pixvod_status batch_track_impl(pixvod_batch* b, int n_iters) {
+    pixvod_status s;
+    if (b->schedule == PIXVOD_SCHED_PLAIN) {
+        for (int i = 0; i < b->n; ++i) {
+            pixvod_handle* h = &b->seq[i];
+            int64_t before = h->launches;
+            s = track_impl<T>(h, b->frames[i], b->normals[i], n_iters);
+            b->launches += h->launches - before;
+            if (s != PIXVOD_OK) return s;
+        }
+        b->frame_index++;
+        return PIXVOD_OK;
+    }
+    if (b->frame_index == 0) {
+        if ((s = batch_keyframe<T>(b)) != PIXVOD_OK) return s;
+        for (auto& h : b->seq) {
+            h.frame_index = 1;
+            h.has_target = false;
+        }
+        b->frame_index = 1;
+        return PIXVOD_OK;
+    }
+    const bool kf = b->p.kf_interval > 0 && b->frame_index % b->p.kf_interval == 0;
+    pv::k_batch_ingest_target<T><<<b->n_work, pixel_block(), 0, b->stream>>>(descs<T>(b), works(b));
+    if ((s = batch_launched(b)) != PIXVOD_OK) return s;
+    if ((s = batch_sweeps<T>(b, n_iters, b->schedule)) != PIXVOD_OK) return s;
+    pv::k_batch_reduce<T><<<b->n_work, pv::RED_THREADS, 0, b->stream>>>(descs<T>(b), works(b), b->seq[0].cur,
+                                                                         kf ? 1 : 0);
+    if ((s = batch_launched(b)) != PIXVOD_OK) return s;
+    if (kf && (s = batch_keyframe<T>(b)) != PIXVOD_OK) return s;
+    for (auto& h : b->seq) {
+        h.frame_index++;
+        h.has_target = !kf;
+    }
+    b->frame_index++;
+    return PIXVOD_OK;
+}
+
+template <typename T>
+pixvod_status batch_autotune_impl(pixvod_batch* b, int n_iters, int reps, float* times) {
+    // candidates: plain, batched, persistent 2/3/4 blocks per SM
+    const int sched[5] = {PIXVOD_SCHED_PLAIN, PIXVOD_SCHED_BATCHED, PIXVOD_SCHED_PERSISTENT,
+                          PIXVOD_SCHED_PERSISTENT, PIXVOD_SCHED_PERSISTENT};
+    const int bps[5] = {0, 0, 2, 3, 4};
+    const int keep_bps = b->blocks_per_sm;
+    cudaEvent_t e0, e1;
+    pixvod_status s = cuda_status(cudaEventCreate(&e0));
+    if (s != PIXVOD_OK) return s;
+    if ((s = cuda_status(cudaEventCreate(&e1))) != PIXVOD_OK) {
+        cudaEventDestroy(e0);
+        return s;
+    }
+    // each sequence tracks its keyframe against itself
+    pv::k_batch_ingest_target<T><<<b->n_work, pixel_block(), 0, b->stream>>>(descs<T>(b), works(b));
+    s = batch_launched(b);
+    float best = -1.f;
+    int best_k = 4;
+    for (int k = 0; k < 5 && s == PIXVOD_OK; ++k) {
+        if (sched[k] == PIXVOD_SCHED_PERSISTENT && bps[k] > b->max_blocks_per_sm) {
+            if (times) times[k] = -1.f;
+            continue;
+        }
+        b->blocks_per_sm = bps[k] > 0 ? bps[k] : keep_bps;
+        float total = 0.f;
+        for (int r = 0; r <= reps && s == PIXVOD_OK; ++r) {  // run 0 warms up
+            cudaEventRecord(e0, b->stream);
+            if (sched[k] == PIXVOD_SCHED_PLAIN) {
+                for (int i = 0; i < b->n && s == PIXVOD_OK; ++i) {
+                    pixvod_handle* h = &b->seq[i];
+                    int64_t before = h->launches;
+                    s = run_sweeps<T>(h, n_iters);
+                    b->launches += h->launches - before;
+                }
+            } else {
+                s = batch_sweeps<T>(b, n_iters, sched[k]);
+            }
+            cudaEventRecord(e1, b->stream);
+            if (s == PIXVOD_OK) s = cuda_status(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) total += ms;
+            if (s == PIXVOD_OK) s = batch_keyframe<T>(b);  // back to the keyframe state
+        }
+        float mean = total / (reps > 0 ? reps : 1);
+        if (times) times[k] = mean;
+        if (s == PIXVOD_OK && (best < 0.f || mean < best)) {
+            best = mean;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != PIXVOD_OK) return s;
+    b->schedule = sched[best_k];
+    b->blocks_per_sm = bps[best_k] > 0 ? bps[best_k] : keep_bps;
+    return cuda_status(cudaStreamSynchronize(b->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+pixvod_status pixvod_batch_workspace_bytes(int32_t n, const pixvod_intrinsics* K, const pixvod_params* p,
+                                           size_t* out_bytes) {
+    if (n < 1 || !K || !params_ok(p) || !out_bytes) return PIXVOD_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!intrinsics_ok(&K[i])) return PIXVOD_EINVAL;
+    *out_bytes = make_batch_layout(n, K, p).total;
+    return PIXVOD_OK;
+}
+
+pixvod_status pixvod_batch_create(int32_t n, const pixvod_intrinsics* K, const pixvod_params* p, void* d_workspace,
+                                  size_t ws_bytes, void* stream, pixvod_batch** out) {
+    if (!out) return PIXVOD_EINVAL;
+    *out = nullptr;
+    size_t need = 0;
+    pixvod_status s = pixvod_batch_workspace_bytes(n, K, p, &need);
+    if (s != PIXVOD_OK) return s;
+    if (!d_workspace || !aligned(d_workspace, kAlign)) return PIXVOD_EINVAL;
+    if (ws_bytes < need) return PIXVOD_ENOMEM;
+    BatchLayout B = make_batch_layout(n, K, p);
+    pixvod_batch* b = new (std::nothrow) pixvod_batch();
+    if (!b) return PIXVOD_ENOMEM;
+    b->n = n;
+    b->p = *p;
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->ws = static_cast<char*>(d_workspace);
+    b->off_desc = B.off_desc;
+    b->off_work = B.off_work;
+    b->off_sync = B.off_sync;
+    b->n_work = B.n_work;
+    b->schedule = PIXVOD_SCHED_PERSISTENT;
+    b->inputs_set = false;
+    b->frames.assign(n, nullptr);
+    b->normals.assign(n, nullptr);
+    b->frame_index = 0;
+    b->launches = 0;
+    b->seq.resize(n);
+    for (int i = 0; i < n; ++i) {
+        pixvod_handle& h = b->seq[i];
+        h.K = K[i];
+        h.p = *p;
+        h.L = B.seq[i];
+        h.ws = b->ws + B.off_seq[i];
+        h.stream = b->stream;
+        h.cur = 0;
+        h.frame_index = 0;
+        h.has_target = false;
+        h.launches = 0;
+        h.profiling = false;
+        h.ev_used = 0;
+        h.prof_sweeps = 0;
+        h.prof_ms = 0;
+        h.prof_launch_base = 0;
+    }
+    int dev = 0;
+    s = cuda_status(cudaGetDevice(&dev));
+    if (s == PIXVOD_OK) s = cuda_status(cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    int coop = 0;
+    if (s == PIXVOD_OK) s = cuda_status(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (s == PIXVOD_OK) s = cuda_status(p->precision == 64 ? sweep_attributes<double>() : sweep_attributes<float>());
+    if (s == PIXVOD_OK) {
+        int m = 0;
+        s = cuda_status(p->precision == 64
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pv::k_sweeps<double>,
+                                                                            pv::SWEEP_THREADS,
+                                                                            pv::sweep_smem_bytes<double>())
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pv::k_sweeps<float>,
+                                                                            pv::SWEEP_THREADS,
+                                                                            pv::sweep_smem_bytes<float>()));
+        b->max_blocks_per_sm = coop ? (m < 4 ? m : 4) : 0;
+        b->blocks_per_sm = b->max_blocks_per_sm;
+        if (b->max_blocks_per_sm < 1) b->schedule = PIXVOD_SCHED_BATCHED;
+    }
+    if (s == PIXVOD_OK) s = cuda_status(cudaMemsetAsync(b->ws, 0, B.total, b->stream));
+    double eye[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+    for (int i = 0; i < n && s == PIXVOD_OK; ++i) {
+        Scalars* sc = scalars(&b->seq[i]);
+        s = cuda_status(cudaMemcpyAsync(sc->T_kf, eye, sizeof(eye), cudaMemcpyHostToDevice, b->stream));
+        if (s == PIXVOD_OK)
+            s = cuda_status(cudaMemcpyAsync(sc->T_cur, eye, sizeof(eye), cudaMemcpyHostToDevice, b->stream));
+        if (s == PIXVOD_OK) s = upload_desc(&b->seq[i]);  // for the plain schedule
+        if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(b->stream));  // eye outlives the copies
+    }
+    if (s == PIXVOD_OK) {
+        std::vector<pv::Work> w;
+        w.reserve(B.n_work);
+        for (int i = 0; i < n; ++i)
+            for (int t = 0; t < B.seq[i].tiles_x * B.seq[i].tiles_y; ++t) w.push_back(pv::Work{i, t});
+        s = cuda_status(cudaMemcpyAsync(b->ws + b->off_work, w.data(), w.size() * sizeof(pv::Work),
+                                        cudaMemcpyHostToDevice, b->stream));
+        if (s == PIXVOD_OK) s = p->precision == 64 ? upload_descs<double>(b) : upload_descs<float>(b);
+        if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(b->stream));
+    }
+    if (s != PIXVOD_OK) {
+        delete b;
+        return s;
+    }
+    *out = b;
+    return PIXVOD_OK;
+}
+
+pixvod_status pixvod_batch_destroy(pixvod_batch* b) {
+    delete b;
+    return PIXVOD_OK;
+}
+
+pixvod_status pixvod_batch_set_inputs(pixvod_batch* b, const float* const* d_frames, const float* const* d_normals) {
+    if (!b || !d_frames || !d_normals) return PIXVOD_EINVAL;
+    for (int i = 0; i < b->n; ++i)
+        if (!d_frames[i] || !d_normals[i] || !aligned(d_frames[i], 4) || !aligned(d_normals[i], 4))
+            return PIXVOD_EINVAL;
+    for (int i = 0; i < b->n; ++i) {
+        b->frames[i] = d_frames[i];
+        b->normals[i] = d_normals[i];
+    }
+    pixvod_status s = b->p.precision == 64 ? upload_descs<double>(b) : upload_descs<float>(b);
+    if (s == PIXVOD_OK) b->inputs_set = true;
+    return s;
+}
+
+pixvod_status pixvod_batch_track(pixvod_batch* b, int32_t n_iters) {
+    if (!b || n_iters < 0) return PIXVOD_EINVAL;
+    if (!b->inputs_set) return PIXVOD_ESTATE;
+    return b->p.precision == 64 ? batch_track_impl<double>(b, n_iters) : batch_track_impl<float>(b, n_iters);
+}
+
+pixvod_status pixvod_batch_get_poses(pixvod_batch* b, double* xi) {
+    if (!b || !xi) return PIXVOD_EINVAL;
+    for (int i = 0; i < b->n; ++i) {
+        pixvod_status s = cuda_status(cudaMemcpyAsync(xi + 6 * i, scalars(&b->seq[i])->xi_est, 6 * sizeof(double),
+                                                      cudaMemcpyDeviceToHost, b->stream));
+        if (s != PIXVOD_OK) return s;
+    }
+    return cuda_status(cudaStreamSynchronize(b->stream));
+}
+
+pixvod_status pixvod_batch_get_status(pixvod_batch* b, uint32_t* flags) {
+    if (!b || !flags) return PIXVOD_EINVAL;
+    std::vector<uint32_t> f(b->n + 1, 0);
+    for (int i = 0; i < b->n; ++i) {
+        pixvod_status s = cuda_status(cudaMemcpyAsync(&f[i], &scalars(&b->seq[i])->flags, sizeof(uint32_t),
+                                                      cudaMemcpyDeviceToHost, b->stream));
+        if (s != PIXVOD_OK) return s;
+    }
+    pixvod_status s = cuda_status(
+        cudaMemcpyAsync(&f[b->n], batch_sync(b) + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->stream));
+    if (s != PIXVOD_OK) return s;
+    if ((s = cuda_status(cudaStreamSynchronize(b->stream))) != PIXVOD_OK) return s;
+    uint32_t all = 0;
+    for (uint32_t x : f) all |= x;
+    *flags = all;
+    return all ? PIXVOD_ENUMERIC : PIXVOD_OK;
+}
+
+pixvod_status pixvod_batch_state_size(pixvod_batch* b, int32_t i, size_t* bytes) {
+    if (!b || i < 0 || i >= b->n) return PIXVOD_EINVAL;
+    return pixvod_state_size(&b->seq[i], bytes);
+}
+
+pixvod_status pixvod_batch_save_state(pixvod_batch* b, int32_t i, void* h_buf, size_t bytes) {
+    if (!b || i < 0 || i >= b->n) return PIXVOD_EINVAL;
+    return pixvod_save_state(&b->seq[i], h_buf, bytes);
+}
+
+pixvod_status pixvod_batch_set_schedule(pixvod_batch* b, int32_t schedule, int32_t blocks_per_sm) {
+    if (!b) return PIXVOD_EINVAL;
+    if (schedule == PIXVOD_SCHED_PERSISTENT) {
+        if (blocks_per_sm < 1 || b->max_blocks_per_sm < 1) return PIXVOD_EINVAL;
+        b->blocks_per_sm = blocks_per_sm < b->max_blocks_per_sm ? blocks_per_sm : b->max_blocks_per_sm;
+    } else if (schedule != PIXVOD_SCHED_PLAIN && schedule != PIXVOD_SCHED_BATCHED) {
+        return PIXVOD_EINVAL;
+    }
+    b->schedule = schedule;
+    return PIXVOD_OK;
+}
+
+pixvod_status pixvod_batch_get_schedule(pixvod_batch* b, int32_t* schedule, int32_t* blocks_per_sm) {
+    if (!b || !schedule || !blocks_per_sm) return PIXVOD_EINVAL;
+    *schedule = b->schedule;
+    *blocks_per_sm = b->blocks_per_sm;
+    return PIXVOD_OK;
+}
+
+pixvod_status pixvod_batch_autotune(pixvod_batch* b, int32_t n_iters, int32_t reps, float* times_ms) {
+    if (!b || n_iters < 1 || reps < 1) return PIXVOD_EINVAL;
+    if (!b->inputs_set || b->frame_index != 1) return PIXVOD_ESTATE;
+    return b->p.precision == 64 ? batch_autotune_impl<double>(b, n_iters, reps, times_ms)
+                                : batch_autotune_impl<float>(b, n_iters, reps, times_ms);
+}
+
+pixvod_status pixvod_batch_launch_count(pixvod_batch* b, int64_t* out) {
+    if (!b || !out) return PIXVOD_EINVAL;
+    *out = b->launches;
     return PIXVOD_OK;
 }
 

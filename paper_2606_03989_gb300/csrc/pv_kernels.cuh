@@ -111,11 +111,9 @@ __device__ __forceinline__ void normal_slopes(const float* __restrict__ n, int u
 // Keyframe: source intensities and the normal-integration edge measurements of
 // Eq. 6 (m_x between (u, v) and (u+1, v), m_y between (u, v) and (u, v+1)).
 template <typename T>
-__global__ void k_ingest_keyframe(Geometry<T> g, const float* __restrict__ frame,
-                                  const float* __restrict__ normals, T* I_s, T* m_x, T* m_y) {
-    int u = blockIdx.x * blockDim.x + threadIdx.x;
-    int v = blockIdx.y * blockDim.y + threadIdx.y;
-    if (u >= g.W || v >= g.H) return;
+__device__ __forceinline__ void ingest_keyframe_px(const Geometry<T>& g, const float* __restrict__ frame,
+                                                   const float* __restrict__ normals, T* I_s, T* m_x, T* m_y,
+                                                   int u, int v) {
     size_t i = (size_t)v * g.pitch + u;
     size_t f = (size_t)v * g.W + u;
     I_s[i] = T(frame[f]);
@@ -136,12 +134,19 @@ __global__ void k_ingest_keyframe(Geometry<T> g, const float* __restrict__ frame
     m_y[i] = my;
 }
 
-// Target: intensities and central-difference gradients (replicated borders).
 template <typename T>
-__global__ void k_ingest_target(Geometry<T> g, const float* __restrict__ frame, T* I_t, T* g_x, T* g_y) {
+__global__ void k_ingest_keyframe(Geometry<T> g, const float* __restrict__ frame,
+                                  const float* __restrict__ normals, T* I_s, T* m_x, T* m_y) {
     int u = blockIdx.x * blockDim.x + threadIdx.x;
     int v = blockIdx.y * blockDim.y + threadIdx.y;
     if (u >= g.W || v >= g.H) return;
+    ingest_keyframe_px(g, frame, normals, I_s, m_x, m_y, u, v);
+}
+
+// Target: intensities and central-difference gradients (replicated borders).
+template <typename T>
+__device__ __forceinline__ void ingest_target_px(const Geometry<T>& g, const float* __restrict__ frame, T* I_t,
+                                                 T* g_x, T* g_y, int u, int v) {
     size_t i = (size_t)v * g.pitch + u;
     const float* row = frame + (size_t)v * g.W;
     int ul = u > 0 ? u - 1 : 0, ur = u + 1 < g.W ? u + 1 : g.W - 1;
@@ -151,13 +156,19 @@ __global__ void k_ingest_target(Geometry<T> g, const float* __restrict__ frame, 
     g_y[i] = T(0.5) * (T(frame[(size_t)vd * g.W + u]) - T(frame[(size_t)vu * g.W + u]));
 }
 
-// Keyframe reset: identity pose, log-depth at the segment's prior mean, no
-// messages, belief equal to the priors (M_p = lam_P I, u = 0, s = lam_Z).
 template <typename T>
-__global__ void k_reset(Geometry<T> g, Factors<T> f, T* state, const Scalars* sc) {
+__global__ void k_ingest_target(Geometry<T> g, const float* __restrict__ frame, T* I_t, T* g_x, T* g_y) {
     int u = blockIdx.x * blockDim.x + threadIdx.x;
     int v = blockIdx.y * blockDim.y + threadIdx.y;
     if (u >= g.W || v >= g.H) return;
+    ingest_target_px(g, frame, I_t, g_x, g_y, u, v);
+}
+
+// Keyframe reset: identity pose, log-depth at the segment's prior mean, no
+// messages, belief equal to the priors (M_p = lam_P I, u = 0, s = lam_Z).
+template <typename T>
+__device__ __forceinline__ void reset_px(const Geometry<T>& g, const Factors<T>& f, T* state, const Scalars* sc,
+                                         int u, int v) {
     T* st = state + state_index(u, v, g.tiles_x);
     T d0 = T(sc->d_prior);
     for (int p = 0; p < N_PLANES; ++p) st[p * TILE_PX] = T(0);
@@ -165,6 +176,14 @@ __global__ void k_reset(Geometry<T> g, Factors<T> f, T* state, const Scalars* sc
 #pragma unroll
     for (int k = 0; k < 6; ++k) st[(PL_MP + pidx(k, k)) * TILE_PX] = f.lam_P;
     st[PL_S * TILE_PX] = f.lam_Z;
+}
+
+template <typename T>
+__global__ void k_reset(Geometry<T> g, Factors<T> f, T* state, const Scalars* sc) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = blockIdx.y * blockDim.y + threadIdx.y;
+    if (u >= g.W || v >= g.H) return;
+    reset_px(g, f, state, sc, u, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -216,6 +235,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
+// Loads of the swept state bypass L1 (ld.global.cg): the persistent batched
+// kernel reads, after a grid barrier, data other SMs wrote in the same launch,
+// and an SM's L1 is not kept coherent with those writes.
+template <typename T>
+__device__ __forceinline__ T ld_state(const T* p) {
+    return __ldcg(p);
+}
+
 // Thread block of the sweep kernel: one state tile (32 x 4 pixels), one thread
 // per pixel; 4 blocks per SM (55 KB of shared memory and at most 128 registers
 // each). Each thread keeps its four damped identity messages in shared memory
@@ -230,25 +257,26 @@ constexpr size_t sweep_smem_bytes() {
     return sizeof(T) * MSG_PLANES * TILE_PX;
 }
 
+// One synchronous sweep over one state tile (tx, ty) by the calling block. The
+// block must have initialised `bar` (one arrival); `parity` is the phase this
+// tile's bulk copy completes. The caller synchronises the block before reusing
+// `msg` for another tile.
 template <typename T>
-__global__ void __launch_bounds__(SWEEP_THREADS, 4) k_sweep(const SweepArgs<T> a) {
-    // msg[p * TILE_PX + tid]: this tile's 108 identity-message planes, bulk-copied
-    // in at the start (the old messages), overwritten in place by the damped new ones
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    T* msg = reinterpret_cast<T*>(smem_raw);
+__device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty, T* msg, uint64_t* bar,
+                                           unsigned parity) {
     const int tid = threadIdx.y * SWEEP_BX + threadIdx.x;
-    const int u = blockIdx.x * SWEEP_BX + threadIdx.x;
-    const int v = blockIdx.y * SWEEP_BY + threadIdx.y;
+    const int u = tx * SWEEP_BX + threadIdx.x;
+    const int v = ty * SWEEP_BY + threadIdx.y;
     const Geometry<T>& g = a.g;
     const Factors<T>& F = a.f;
-    const size_t tile = (size_t)blockIdx.y * g.tiles_x + blockIdx.x;
-    if (tid == 0) mbar_init(&bar, 1);
-    __syncthreads();
+    const size_t tile = (size_t)ty * g.tiles_x + tx;
     if (tid == 0) {
+        // order earlier generic-proxy accesses (global stores of a previous sweep in
+        // the same launch, shared-memory use of a previous tile) before the async copy
+        asm volatile("fence.proxy.async;" ::: "memory");
         constexpr unsigned bytes = sizeof(T) * MSG_PLANES * TILE_PX;
-        mbar_expect_tx(&bar, bytes);
-        bulk_copy_g2s(msg, a.in + tile * TILE_WORDS + PL_ID * TILE_PX, bytes, &bar);
+        mbar_expect_tx(bar, bytes);
+        bulk_copy_g2s(msg, a.in + tile * TILE_WORDS + PL_ID * TILE_PX, bytes, bar);
     }
     if (u >= g.W || v >= g.H) return;
     const int i = v * g.pitch + u;
@@ -257,8 +285,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) k_sweep(const SweepArgs<T> a
 
     T xi[6], d;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) xi[k] = Si[k * TILE_PX];
-    d = Si[6 * TILE_PX];
+    for (int k = 0; k < 6; ++k) xi[k] = ld_state(Si + k * TILE_PX);
+    d = ld_state(Si + 6 * TILE_PX);
     T R[9], t[3];
     se3_exp(xi, R, t);
 
@@ -341,10 +369,10 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) k_sweep(const SweepArgs<T> a
 
     // --- a2/a3: pairwise messages from the four neighbours ---
     unsigned flags = 0;
-    if (!mbar_wait_bounded(&bar, 0)) {
+    if (!mbar_wait_bounded(bar, parity)) {
         // the tile's messages never arrived: flag it, wait once more, leave the tile
         atomicOr(&a.sc->flags, FLAG_TIMEOUT);
-        mbar_wait_bounded(&bar, 0);
+        mbar_wait_bounded(bar, parity);
         return;
     }
     const T beta = F.beta, omb = T(1) - F.beta;
@@ -367,7 +395,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) k_sweep(const SweepArgs<T> a
         {
             T xj[6];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) xj[q] = Sj[q * TILE_PX];
+            for (int q = 0; q < 6; ++q) xj[q] = ld_state(Sj + q * TILE_PX);
             T Rj[9], tj[3], Rr[9], tr[3];
             se3_exp(xj, Rj, tj);
             se3_invmul(Rj, tj, R, t, Rr, tr);
@@ -379,18 +407,18 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) k_sweep(const SweepArgs<T> a
         T W[21], C[21], uj[6], gv[6];
 #pragma unroll
         for (int q = 0; q < 21; ++q) {
-            W[q] = Sj[(PL_MP + q) * TILE_PX] - mj[q * TILE_PX];
+            W[q] = ld_state(Sj + (PL_MP + q) * TILE_PX) - ld_state(mj + q * TILE_PX);
             C[q] = W[q];
         }
 #pragma unroll
-        for (int q = 0; q < 6; ++q) uj[q] = Sj[(PL_U + q) * TILE_PX];
+        for (int q = 0; q < 6; ++q) uj[q] = ld_state(Sj + (PL_U + q) * TILE_PX);
         // g0 = eta_v - W r with eta_v = -eta_{f->j}
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             T wr = T(0);
 #pragma unroll
             for (int c = 0; c < 6; ++c) wr += W[pidx(q, c)] * rb[c];
-            gv[q] = -mj[(21 + q) * TILE_PX] - wr;
+            gv[q] = -ld_state(mj + (21 + q) * TILE_PX) - wr;
         }
         // A = W + lam_R I is well conditioned (W is bounded by a few lam_R)
 #pragma unroll
@@ -447,15 +475,15 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) k_sweep(const SweepArgs<T> a
         }
 
         // normal-integration factor (Eq. 6): r_i = d_i - d_j + sg m
-        T dj = Sj[6 * TILE_PX];
-        T sv = Sj[PL_S * TILE_PX] - Sj[(PL_NM + 2 * ko) * TILE_PX];
-        T evn = -Sj[(PL_NM + 2 * ko + 1) * TILE_PX];
+        T dj = ld_state(Sj + 6 * TILE_PX);
+        T sv = ld_state(Sj + PL_S * TILE_PX) - ld_state(Sj + (PL_NM + 2 * ko) * TILE_PX);
+        T evn = -ld_state(Sj + (PL_NM + 2 * ko + 1) * TILE_PX);
         T m = k == 0 ? a.m_x[i - 1] : (k == 1 ? a.m_x[i] : (k == 2 ? a.m_y[i - g.pitch] : a.m_y[i]));
         T sg = (k == 0 || k == 2) ? T(1) : T(-1);
         T rn = d - dj + sg * m;
         T den = v_div(T(1), F.lam_N + sv);
-        T nnew = omb * (F.lam_N * sv * den) + beta * Si[(PL_NM + 2 * k) * TILE_PX];
-        T enew = omb * (F.lam_N * (evn - sv * rn) * den) + beta * Si[(PL_NM + 2 * k + 1) * TILE_PX];
+        T nnew = omb * (F.lam_N * sv * den) + beta * ld_state(Si + (PL_NM + 2 * k) * TILE_PX);
+        T enew = omb * (F.lam_N * (evn - sv * rn) * den) + beta * ld_state(Si + (PL_NM + 2 * k + 1) * TILE_PX);
         md += nnew;
         eb[6] += enew;
         if (k == 0) { nl0 = nnew; ne0 = enew; }
@@ -572,13 +600,12 @@ constexpr int RED_THREADS = TILE_PX;
 // writes xi_est and the mean log-depth, composes T_cur = Exp(xi_est) T_kf and,
 // at an anchoring frame, moves the keyframe: T_kf <- T_cur, d_prior <- d_mean.
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_reduce(Geometry<T> g, const T* __restrict__ state,
-                                                        double* __restrict__ partials, Scalars* sc,
-                                                        int anchor) {
+__device__ __forceinline__ void reduce_tile(const Geometry<T>& g, const T* __restrict__ state,
+                                            double* __restrict__ partials, Scalars* sc, int anchor, int tile,
+                                            int n_tiles) {
     __shared__ double sh[7][RED_THREADS];
     __shared__ bool last;
     const int tid = threadIdx.x;
-    const int tile = blockIdx.x;
     const int u = (tile % g.tiles_x) * TILE_W + tid % TILE_W;
     const int v = (tile / g.tiles_x) * TILE_H + tid / TILE_W;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -600,12 +627,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(Geometry<T> g, const T* 
 #pragma unroll
         for (int q = 0; q < 7; ++q) partials[tile * 7 + q] = sh[q][0];
         __threadfence();
-        last = atomicAdd(&sc->counter, 1u) == (unsigned)(gridDim.x - 1);
+        last = atomicAdd(&sc->counter, 1u) == (unsigned)(n_tiles - 1);
     }
     __syncthreads();
     if (!last) return;
     double r[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int h = tid; h < (int)gridDim.x; h += RED_THREADS)
+    for (int h = tid; h < n_tiles; h += RED_THREADS)
 #pragma unroll
         for (int q = 0; q < 7; ++q) r[q] += __ldcg(partials + h * 7 + q);
 #pragma unroll
@@ -641,6 +668,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(Geometry<T> g, const T* 
         }
         sc->counter = 0;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce(Geometry<T> g, const T* __restrict__ state,
+                                                        double* __restrict__ partials, Scalars* sc,
+                                                        int anchor) {
+    reduce_tile(g, state, partials, sc, anchor, blockIdx.x, gridDim.x);
 }
 
 // Depth output: exp(sign * mu_6) as dense float32.

@@ -159,3 +159,97 @@ class Tracker:
         n = ctypes.c_int64(0)
         nat.check(nat.lib.pixvod_launch_count(self._h, ctypes.byref(n)), "pixvod_launch_count")
         return n.value
+
+
+class Batch:
+    """Many sequences (own intrinsics and state, shared params) advanced together.
+
+    ``set_inputs`` registers one frame buffer and one normals buffer per
+    sequence (CUDA tensors); ``track(n_iters)`` consumes what they hold."""
+
+    def __init__(self, Ks, params=None, device=None, stream=None):
+        import torch
+        self._torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("PixVOD needs a CUDA device; no CPU implementation exists")
+        self.K = [k if isinstance(k, nat.pixvod_intrinsics) else nat.intrinsics(*k) for k in Ks]
+        self.n = len(self.K)
+        self.params = params if params is not None else nat.params_default()
+        self.device = torch.device(device if device is not None else "cuda")
+        arr = (nat.pixvod_intrinsics * self.n)(*self.K)
+        self._karr = arr
+        need = ctypes.c_size_t(0)
+        nat.check(nat.lib.pixvod_batch_workspace_bytes(self.n, ctypes.cast(arr, ctypes.c_void_p),
+                                                        ctypes.byref(self.params), ctypes.byref(need)),
+                  "pixvod_batch_workspace_bytes")
+        self._ws = torch.empty(need.value + 256, dtype=torch.uint8, device=self.device)
+        ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        nat.check(nat.lib.pixvod_batch_create(self.n, ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(self.params),
+                                              ptr, need.value, self.stream.cuda_stream, ctypes.byref(h)),
+                  "pixvod_batch_create")
+        self._h = h
+        self._inputs = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            nat.lib.pixvod_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_inputs(self, frames, normals):
+        assert len(frames) == self.n and len(normals) == self.n
+        fp = (ctypes.c_void_p * self.n)(*[f.data_ptr() for f in frames])
+        npp = (ctypes.c_void_p * self.n)(*[x.data_ptr() for x in normals])
+        nat.check(nat.lib.pixvod_batch_set_inputs(self._h, ctypes.cast(fp, ctypes.c_void_p),
+                                                  ctypes.cast(npp, ctypes.c_void_p)), "pixvod_batch_set_inputs")
+        self._inputs = (list(frames), list(normals))   # keep the buffers alive
+
+    def track(self, n_iters: int = 20):
+        nat.check(nat.lib.pixvod_batch_track(self._h, int(n_iters)), "pixvod_batch_track")
+
+    def poses(self) -> np.ndarray:
+        xi = np.zeros((self.n, 6))
+        nat.check(nat.lib.pixvod_batch_get_poses(self._h, xi.ctypes.data), "pixvod_batch_get_poses")
+        return xi
+
+    def status(self) -> int:
+        flags = ctypes.c_uint32(0)
+        st = nat.lib.pixvod_batch_get_status(self._h, ctypes.byref(flags))
+        if st not in (nat.OK, nat.ENUMERIC):
+            nat.check(st, "pixvod_batch_get_status")
+        return flags.value
+
+    def save_state(self, i: int) -> bytes:
+        n = ctypes.c_size_t(0)
+        nat.check(nat.lib.pixvod_batch_state_size(self._h, int(i), ctypes.byref(n)), "pixvod_batch_state_size")
+        buf = ctypes.create_string_buffer(n.value)
+        nat.check(nat.lib.pixvod_batch_save_state(self._h, int(i), buf, n.value), "pixvod_batch_save_state")
+        return buf.raw
+
+    def state(self, i: int) -> nat.StateView:
+        return nat.parse_state(self.save_state(i))
+
+    def set_schedule(self, schedule: int, blocks_per_sm: int = 4):
+        nat.check(nat.lib.pixvod_batch_set_schedule(self._h, int(schedule), int(blocks_per_sm)),
+                  "pixvod_batch_set_schedule")
+
+    def schedule(self):
+        s, b = ctypes.c_int32(0), ctypes.c_int32(0)
+        nat.check(nat.lib.pixvod_batch_get_schedule(self._h, ctypes.byref(s), ctypes.byref(b)),
+                  "pixvod_batch_get_schedule")
+        return s.value, b.value
+
+    def autotune(self, n_iters: int = 20, reps: int = 2):
+        times = (ctypes.c_float * 5)()
+        nat.check(nat.lib.pixvod_batch_autotune(self._h, int(n_iters), int(reps), ctypes.cast(times, ctypes.c_void_p)),
+                  "pixvod_batch_autotune")
+        names = ["plain", "batched", "persistent2", "persistent3", "persistent4"]
+        return dict(zip(names, list(times))), self.schedule()
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int64(0)
+        nat.check(nat.lib.pixvod_batch_launch_count(self._h, ctypes.byref(n)), "pixvod_batch_launch_count")
+        return n.value
