@@ -298,12 +298,148 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty
     T eb[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) eb[q] = T(0);
+    // --- priors (Eq. 4 with identity Jacobian; log-depth prior) ---
+    T Mp[21];
+#pragma unroll
+    for (int q = 0; q < 21; ++q) Mp[q] = T(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        Mp[pidx(k, k)] = F.lam_P;
+        eb[k] -= F.lam_P * xi[k];
+    }
+    T md = F.lam_Z;
+    eb[6] -= F.lam_Z * (d - T(a.sc->d_prior));
+
+    // --- a2/a3: pairwise messages from the four neighbours ---
+    unsigned flags = 0;
+    if (!mbar_wait_bounded(bar, parity)) {
+        // the tile's messages never arrived: flag it, wait once more, leave the tile
+        atomicOr(&a.sc->flags, FLAG_TIMEOUT);
+        mbar_wait_bounded(bar, parity);
+        return;
+    }
+    const T beta = F.beta, omb = T(1) - F.beta;
+    T nl0 = T(0), ne0 = T(0), nl1 = T(0), ne1 = T(0), nl2 = T(0), ne2 = T(0), nl3 = T(0), ne3 = T(0);
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        T* mb = msg + (k * ID_STRIDE) * TILE_PX + tid;          // identity slot k
+        const int un = u + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+        const int vn = v + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+        const bool has = un >= 0 && un < g.W && vn >= 0 && vn < g.H;
+        if (!has) {
+#pragma unroll
+            for (int q = 0; q < ID_STRIDE; ++q) mb[q * TILE_PX] = T(0);
+            continue;
+        }
+        const int ko = k ^ 1;
+        const T* Sj = a.in + state_index(un, vn, g.tiles_x);
+        // identity factor (Eq. 5): r = Log(Exp(xi_j)^-1 Exp(xi_i)), J_i = I, J_j = -I
+        T rb[6];
+        {
+            T xj[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) xj[q] = ld_state(Sj + q * TILE_PX);
+            T Rj[9], tj[3], Rr[9], tr[3];
+            se3_exp(xj, Rj, tj);
+            se3_invmul(Rj, tj, R, t, Rr, tr);
+            se3_log(Rr, tr, rb);
+        }
+        // variable-to-factor marginal of j: V = W + u u^T with W = M_p,j - Lambda_{f->j}
+        // (pose prior plus j's three other identity messages) and u = u_j
+        const T* mj = Sj + (PL_ID + ID_STRIDE * ko) * TILE_PX;
+        T W[21], C[21], z[6], gv[6];
+        T uz = T(0), ur = T(0), uh = T(0);
+        {
+            T uj[6];
+#pragma unroll
+            for (int q = 0; q < 21; ++q) {
+                W[q] = ld_state(Sj + (PL_MP + q) * TILE_PX) - ld_state(mj + q * TILE_PX);
+                C[q] = W[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q) uj[q] = ld_state(Sj + (PL_U + q) * TILE_PX);
+            // g0 = eta_v - W r with eta_v = -eta_{f->j}
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                T wr = T(0);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) wr += W[pidx(q, c)] * rb[c];
+                gv[q] = -ld_state(mj + (21 + q) * TILE_PX) - wr;
+            }
+            // A = W + lam_R I is well conditioned (its eigenvalues are at least lam_R);
+            // the rank-one u u^T, which can be far larger, stays out of the factorisation
+#pragma unroll
+            for (int q = 0; q < 6; ++q) C[pidx(q, q)] += F.lam_R;
+            T idg0[6];
+            if (!chol_packed<6>(C, idg0)) flags |= FLAG_NONPOS_PIVOT;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) z[q] = uj[q];
+            fwd_solve<6>(C, idg0, z);
+            bwd_solve<6>(C, idg0, z);   // z = A^-1 u
+            fwd_solve<6>(C, idg0, gv);
+            bwd_solve<6>(C, idg0, gv);  // h = A^-1 g0
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                uz += uj[q] * z[q];
+                ur += uj[q] * rb[q];
+                uh += uj[q] * gv[q];
+                C[pidx(q, q)] = idg0[q];  // keep 1/L_qq on the diagonal (the solves below read it there)
+            }
+        }
+        const T iuz = v_div(T(1), T(1) + uz);
+        const T crank = F.lam_R * F.lam_R * iuz;
+        // with C = A + u u^T (Sherman-Morrison):
+        // eta_msg = lam_R C^-1 (eta_v - V r) = lam_R (h - z (u^T r + u^T h) / (1 + u^T z))
+        const T ecoef = (ur + uh) * iuz;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            T e = omb * (F.lam_R * (gv[q] - ecoef * z[q])) + beta * mb[(21 + q) * TILE_PX];
+            eb[q] += e;
+            mb[(21 + q) * TILE_PX] = e;
+        }
+        // Lambda_msg = lam_R C^-1 V = lam_R A^-1 W + lam_R^2 / (1 + u^T z) z z^T, the first
+        // term (equal to W - W A^-1 W) one column at a time, rows c..5 of column c; this
+        // product form has no cancellation for W << lam_R (~ W) or W >> lam_R (~ lam_R I)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            T x[6];
+#pragma unroll
+            for (int r = 0; r < 6; ++r) x[r] = W[pidx(r, c)];
+            fwd_solve_id<6>(C, x);
+            bwd_solve_id<6>(C, x);
+#pragma unroll
+            for (int r = c; r < 6; ++r) {
+                T l = omb * (F.lam_R * x[r] + crank * z[r] * z[c]) + beta * mb[pidx(r, c) * TILE_PX];
+                Mp[pidx(r, c)] += l;
+                mb[pidx(r, c) * TILE_PX] = l;
+            }
+        }
+
+        // normal-integration factor (Eq. 6): r_i = d_i - d_j + sg m
+        T dj = ld_state(Sj + 6 * TILE_PX);
+        T sv = ld_state(Sj + PL_S * TILE_PX) - ld_state(Sj + (PL_NM + 2 * ko) * TILE_PX);
+        T evn = -ld_state(Sj + (PL_NM + 2 * ko + 1) * TILE_PX);
+        T m = k == 0 ? a.m_x[i - 1] : (k == 1 ? a.m_x[i] : (k == 2 ? a.m_y[i - g.pitch] : a.m_y[i]));
+        T sg = (k == 0 || k == 2) ? T(1) : T(-1);
+        T rn = d - dj + sg * m;
+        T den = v_div(T(1), F.lam_N + sv);
+        T nnew = omb * (F.lam_N * sv * den) + beta * ld_state(Si + (PL_NM + 2 * k) * TILE_PX);
+        T enew = omb * (F.lam_N * (evn - sv * rn) * den) + beta * ld_state(Si + (PL_NM + 2 * k + 1) * TILE_PX);
+        md += nnew;
+        eb[6] += enew;
+        if (k == 0) { nl0 = nnew; ne0 = enew; }
+        else if (k == 1) { nl1 = nnew; ne1 = enew; }
+        else if (k == 2) { nl2 = nnew; ne2 = enew; }
+        else { nl3 = nnew; ne3 = enew; }
+    }
+
     T alpha = T(0), rph = T(0);
     T J[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) J[q] = T(0);
 
-    // --- a1: photometric factor (Eqs. 2, 3) at the current mean ---
+    // --- a1: photometric factor (Eqs. 2, 3) at the current mean (it enters only
+    // the belief below, so it is evaluated after the pairwise messages) ---
     {
         T z = v_exp(d);
         T Xs[3] = {z * (T(u) - g.cx) * g.ifx, z * (T(v) - g.cy) * g.ify, z};
@@ -355,143 +491,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty
             rph = r;
         }
     }
-    // --- priors (Eq. 4 with identity Jacobian; log-depth prior) ---
-    T Mp[21];
-#pragma unroll
-    for (int q = 0; q < 21; ++q) Mp[q] = T(0);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        Mp[pidx(k, k)] = F.lam_P;
-        eb[k] -= F.lam_P * xi[k];
-    }
-    T md = F.lam_Z;
-    eb[6] -= F.lam_Z * (d - T(a.sc->d_prior));
-
-    // --- a2/a3: pairwise messages from the four neighbours ---
-    unsigned flags = 0;
-    if (!mbar_wait_bounded(bar, parity)) {
-        // the tile's messages never arrived: flag it, wait once more, leave the tile
-        atomicOr(&a.sc->flags, FLAG_TIMEOUT);
-        mbar_wait_bounded(bar, parity);
-        return;
-    }
-    const T beta = F.beta, omb = T(1) - F.beta;
-    T nl0 = T(0), ne0 = T(0), nl1 = T(0), ne1 = T(0), nl2 = T(0), ne2 = T(0), nl3 = T(0), ne3 = T(0);
-#pragma unroll 1
-    for (int k = 0; k < 4; ++k) {
-        T* mb = msg + (k * ID_STRIDE) * TILE_PX + tid;          // identity slot k
-        const int un = u + (k == 0 ? -1 : (k == 1 ? 1 : 0));
-        const int vn = v + (k == 2 ? -1 : (k == 3 ? 1 : 0));
-        const bool has = un >= 0 && un < g.W && vn >= 0 && vn < g.H;
-        if (!has) {
-#pragma unroll
-            for (int q = 0; q < ID_STRIDE; ++q) mb[q * TILE_PX] = T(0);
-            continue;
-        }
-        const int ko = k ^ 1;
-        const T* Sj = a.in + state_index(un, vn, g.tiles_x);
-        // identity factor (Eq. 5): r = Log(Exp(xi_j)^-1 Exp(xi_i)), J_i = I, J_j = -I
-        T rb[6];
-        {
-            T xj[6];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) xj[q] = ld_state(Sj + q * TILE_PX);
-            T Rj[9], tj[3], Rr[9], tr[3];
-            se3_exp(xj, Rj, tj);
-            se3_invmul(Rj, tj, R, t, Rr, tr);
-            se3_log(Rr, tr, rb);
-        }
-        // variable-to-factor marginal of j: V = W + u u^T with W = M_p,j - Lambda_{f->j}
-        // (pose prior plus j's three other identity messages) and u = u_j
-        const T* mj = Sj + (PL_ID + ID_STRIDE * ko) * TILE_PX;
-        T W[21], C[21], uj[6], gv[6];
-#pragma unroll
-        for (int q = 0; q < 21; ++q) {
-            W[q] = ld_state(Sj + (PL_MP + q) * TILE_PX) - ld_state(mj + q * TILE_PX);
-            C[q] = W[q];
-        }
-#pragma unroll
-        for (int q = 0; q < 6; ++q) uj[q] = ld_state(Sj + (PL_U + q) * TILE_PX);
-        // g0 = eta_v - W r with eta_v = -eta_{f->j}
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            T wr = T(0);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) wr += W[pidx(q, c)] * rb[c];
-            gv[q] = -ld_state(mj + (21 + q) * TILE_PX) - wr;
-        }
-        // A = W + lam_R I is well conditioned (W is bounded by a few lam_R)
-#pragma unroll
-        for (int q = 0; q < 6; ++q) C[pidx(q, q)] += F.lam_R;
-        T idg[6];
-        if (!chol_packed<6>(C, idg)) flags |= FLAG_NONPOS_PIVOT;
-        // Lambda_msg = lam_R C^-1 V with C = A + u u^T:
-        //   = W - (L^-1 W)^T (L^-1 W) + lam_R^2 / (1 + u^T z) z z^T,  z = A^-1 u
-        T z[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) z[q] = uj[q];
-        fwd_solve<6>(C, idg, z);
-        bwd_solve<6>(C, idg, z);
-        fwd_solve<6>(C, idg, gv);
-        bwd_solve<6>(C, idg, gv);  // h = A^-1 g0
-        T uz = T(0), ur = T(0), uh = T(0);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            uz += uj[q] * z[q];
-            ur += uj[q] * rb[q];
-            uh += uj[q] * gv[q];
-        }
-        const T iuz = v_div(T(1), T(1) + uz);
-        const T crank = F.lam_R * F.lam_R * iuz;
-        // eta_msg = lam_R C^-1 (eta_v - V r) = lam_R (h - z (u^T r + u^T h) / (1 + u^T z))
-        const T ecoef = (ur + uh) * iuz;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            T e = omb * (F.lam_R * (gv[q] - ecoef * z[q])) + beta * mb[(21 + q) * TILE_PX];
-            eb[q] += e;
-            mb[(21 + q) * TILE_PX] = e;
-        }
-        // Y = L^-1 W in place of W (columns), then Lambda = W - Y^T Y + crank z z^T
-        {
-            T Y[6][6];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-#pragma unroll
-                for (int r = 0; r < 6; ++r) Y[c][r] = W[pidx(r, c)];
-                fwd_solve<6>(C, idg, Y[c]);
-            }
-#pragma unroll
-            for (int r = 0; r < 6; ++r)
-#pragma unroll
-                for (int c = 0; c <= r; ++c) {
-                    T yy = T(0);
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) yy += Y[r][q] * Y[c][q];
-                    T lnew = W[pidx(r, c)] - yy + crank * z[r] * z[c];
-                    T l = omb * lnew + beta * mb[pidx(r, c) * TILE_PX];
-                    Mp[pidx(r, c)] += l;
-                    mb[pidx(r, c) * TILE_PX] = l;
-                }
-        }
-
-        // normal-integration factor (Eq. 6): r_i = d_i - d_j + sg m
-        T dj = ld_state(Sj + 6 * TILE_PX);
-        T sv = ld_state(Sj + PL_S * TILE_PX) - ld_state(Sj + (PL_NM + 2 * ko) * TILE_PX);
-        T evn = -ld_state(Sj + (PL_NM + 2 * ko + 1) * TILE_PX);
-        T m = k == 0 ? a.m_x[i - 1] : (k == 1 ? a.m_x[i] : (k == 2 ? a.m_y[i - g.pitch] : a.m_y[i]));
-        T sg = (k == 0 || k == 2) ? T(1) : T(-1);
-        T rn = d - dj + sg * m;
-        T den = v_div(T(1), F.lam_N + sv);
-        T nnew = omb * (F.lam_N * sv * den) + beta * ld_state(Si + (PL_NM + 2 * k) * TILE_PX);
-        T enew = omb * (F.lam_N * (evn - sv * rn) * den) + beta * ld_state(Si + (PL_NM + 2 * k + 1) * TILE_PX);
-        md += nnew;
-        eb[6] += enew;
-        if (k == 0) { nl0 = nnew; ne0 = enew; }
-        else if (k == 1) { nl1 = nnew; ne1 = enew; }
-        else if (k == 2) { nl2 = nnew; ne2 = enew; }
-        else { nl3 = nnew; ne3 = enew; }
-    }
-
     // --- a4: belief, mean update, tangent projection ---
     // With B = blockdiag(M_p, m_d), h = B^-1 eta_o and z = B^-1 J, Sherman-Morrison
     // gives tau = Lambda_b^-1 eta_b = h - z alpha (r + J^T h) / (1 + alpha J^T z),

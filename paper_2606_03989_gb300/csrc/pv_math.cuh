@@ -273,4 +273,27 @@ __device__ __forceinline__ void bwd_solve(const T* L, const T* inv_diag, T* b) {
     }
 }
 
+// The same two solves with 1/L_ii stored on the diagonal of L in place of L_ii
+// (a factor whose diagonal is only used through its inverse).
+template <int N, typename T>
+__device__ __forceinline__ void fwd_solve_id(const T* L, T* b) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        T v = b[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) v -= L[pidx(i, k)] * b[k];
+        b[i] = v * L[pidx(i, i)];
+    }
+}
+template <int N, typename T>
+__device__ __forceinline__ void bwd_solve_id(const T* L, T* b) {
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        T v = b[i];
+#pragma unroll
+        for (int k = i + 1; k < N; ++k) v -= L[pidx(k, i)] * b[k];
+        b[i] = v * L[pidx(i, i)];
+    }
+}
+
 }  // namespace pv
