@@ -115,7 +115,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("pv_kernels.cuh", "pv_math.cuh"):
+    for f in ("pv_kernels.cuh", "pv_math.cuh", "pv_batch.cuh"):
         with open(os.path.join(ROOT, "paper_2606_03989_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
