@@ -206,6 +206,45 @@ pixvod_status pixvod_get_profile(pixvod_handle* h, pixvod_profile* out);
 pixvod_status pixvod_launch_count(pixvod_handle* h, int64_t* out);
 
 /* ---------------------------------------------------------------------------
+ * Adjoint of the unrolled sweeps of one frame (reverse-mode derivative).
+ *
+ * With recording on, pixvod_track of a target frame also stores the state every
+ * `checkpoint_every` sweeps. pixvod_backward then differentiates a loss
+ * L(xi_est, inverse depth) of that frame's result through its n_iters sweeps
+ * (Eqs. 2-6 with relinearisation, damping, the belief solve, the mean update
+ * and the tangent projection of Sec. 3.4), recomputing each segment of sweeps
+ * from its checkpoint with the sweep kernel. Gradients are truncated at the
+ * frame start: the state carried from earlier frames is a constant. The
+ * derivative is taken in FP64 whatever the handle's precision.
+ * ------------------------------------------------------------------------- */
+
+/* Device bytes of the recording workspace for frames of at most max_iters
+ * sweeps (>= 1) with a checkpoint every checkpoint_every (>= 1) sweeps. */
+pixvod_status pixvod_backward_workspace_bytes(const pixvod_intrinsics* K, const pixvod_params* p,
+                                              int32_t max_iters, int32_t checkpoint_every, size_t* out_bytes);
+
+/* Turns recording on (d_workspace: 256-byte aligned caller device memory of at
+ * least pixvod_backward_workspace_bytes, owned by the caller and valid while
+ * recording is on) or off (d_workspace NULL). While on, pixvod_track of a
+ * target frame with more than max_iters sweeps returns EINVAL. */
+pixvod_status pixvod_set_recording(pixvod_handle* h, void* d_workspace, size_t ws_bytes, int32_t max_iters,
+                                   int32_t checkpoint_every);
+
+/* Gradients of L through the last tracked frame's sweeps. Inputs (device,
+ * FP64): d_grad_xi = dL/dxi_est (6, or NULL for 0), d_grad_invdepth =
+ * dL/d(exp(-mu_6)) per keyframe pixel (width*height row-major, or NULL for 0).
+ * Outputs (device, FP64, overwritten): d_grad_sigmas = dL/d(sigma_D, sigma_N)
+ * (2), d_grad_Is = dL/d(keyframe intensities) and d_grad_It = dL/d(target
+ * frame intensities) (width*height row-major each). check (host, optional,
+ * 2 doubles): the largest relative difference between the derivative's own
+ * recomputation of a pixel update and the sweep kernel's, and the longest
+ * tape. Synchronises the stream. ESTATE if recording is off or the last call
+ * was not a non-anchoring target frame tracked with recording on; ENUMERIC if
+ * a pixel's derivative tape overflowed. */
+pixvod_status pixvod_backward(pixvod_handle* h, const double* d_grad_xi, const double* d_grad_invdepth,
+                              double* d_grad_sigmas, double* d_grad_Is, double* d_grad_It, double* check);
+
+/* ---------------------------------------------------------------------------
  * Batches: many independent sequences (each with its own intrinsics, image size
  * and state, all with the same params) advanced together, one frame per call.
  * Each sequence's results are bit-identical to tracking it alone with

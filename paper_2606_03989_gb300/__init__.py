@@ -14,12 +14,12 @@ _NATIVE = {"ECUDA", "EINVAL", "ENOMEM", "ENUMERIC", "ESTATE", "ETIMEOUT", "FLAG_
            "intrinsics", "lib", "params", "params_default", "parse_state", "status_string",
            "workspace_bytes"}
 
-__all__ = sorted(_NATIVE | {"Tracker", "Batch"})
+__all__ = sorted(_NATIVE | {"Tracker", "Batch", "track_frame"})
 
 
 def __getattr__(name):
     if name in _NATIVE:
         return getattr(importlib.import_module("._native", __name__), name)
-    if name in ("Tracker", "Batch"):
+    if name in ("Tracker", "Batch", "track_frame"):
         return getattr(importlib.import_module(".tracker", __name__), name)
     raise AttributeError(name)

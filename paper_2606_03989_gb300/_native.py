@@ -79,6 +79,10 @@ def _load():
         "pixvod_set_profiling": (S, [H, I32]),
         "pixvod_get_profile": (S, [H, ctypes.POINTER(pixvod_profile)]),
         "pixvod_launch_count": (S, [H, ctypes.POINTER(I64)]),
+        "pixvod_backward_workspace_bytes": (S, [ctypes.POINTER(pixvod_intrinsics), ctypes.POINTER(pixvod_params),
+                                                I32, I32, ctypes.POINTER(ctypes.c_size_t)]),
+        "pixvod_set_recording": (S, [H, P, ctypes.c_size_t, I32, I32]),
+        "pixvod_backward": (S, [H, P, P, P, P, P, P]),
         "pixvod_pose_mean_static": (S, [P, I32, I32, I64, I64, P, P]),
         "pixvod_batch_workspace_bytes": (S, [I32, P, ctypes.POINTER(pixvod_params), ctypes.POINTER(ctypes.c_size_t)]),
         "pixvod_batch_create": (S, [I32, P, ctypes.POINTER(pixvod_params), P, ctypes.c_size_t, P,

@@ -28,7 +28,7 @@ def nvcc_path() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, "pixvod.cu"), os.path.join(CSRC, "pixvod_static.cu")]
+    return [os.path.join(CSRC, f) for f in ("pixvod.cu", "pixvod_adjoint.cu", "pixvod_static.cu")]
 
 
 def build(verbose_ptxas: bool = False, force: bool = False) -> str:
@@ -38,15 +38,35 @@ def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in deps):
         return LIB
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [nvcc_path(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp] + sources()
+    nvcc = nvcc_path()
+    # one object per translation unit, compiled in parallel, then one link
+    objs, procs = [], []
+    for src in sources():
+        obj = os.path.join(LIBDIR, os.path.basename(src) + ".%d.o" % os.getpid())
+        cmd = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c",
+               "-I", os.path.join(ROOT, "include"), "-o", obj, src]
+        if verbose_ptxas:
+            cmd += ["-Xptxas", "-v"]
+        objs.append(obj)
+        procs.append(subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    errors, logs = [], []
+    for src, pr in zip(sources(), procs):
+        out, err = pr.communicate()
+        logs.append(err)
+        if pr.returncode != 0:
+            errors.append("%s:\n%s%s" % (src, out, err))
+    try:
+        if errors:
+            raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
+        res = subprocess.run([nvcc, ARCH, "-shared", "-o", tmp] + objs, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError("nvcc link failed:\n" + res.stdout + res.stderr)
+    finally:
+        for obj in objs:
+            if os.path.exists(obj):
+                os.remove(obj)
     if verbose_ptxas:
-        cmd += ["-Xptxas", "-v"]
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
-    if verbose_ptxas:
-        sys.stderr.write(res.stderr)
+        sys.stderr.write("".join(logs))
     os.replace(tmp, LIB)
     return LIB
 

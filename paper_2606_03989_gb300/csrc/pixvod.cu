@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/pixvod.h"
+#include "pv_adjoint_api.h"
 #include "pv_batch.cuh"
 
 using pv::Factors;
@@ -95,6 +96,52 @@ Layout make_layout(const pixvod_intrinsics* K, const pixvod_params* p) {
     return L;
 }
 
+// Recording for the adjoint (pixvod_set_recording): checkpoints of the state
+// every `every` sweeps, the states of one segment recomputed from a checkpoint,
+// two adjoint states (FP64), descriptors of the recompute launches, the
+// reverse-mode tapes of the adjoint kernel and a few accumulators.
+constexpr int kTapeCap = 16384;           // tape nodes per thread
+constexpr int kAdjSlotsPerSM = 32;        // adjoint threads per SM (one block)
+struct RecLayout {
+    int n_ckpt, every, max_iters, slots;
+    size_t state_bytes, adj_bytes;
+    size_t off_ckpt, off_seg, off_adj[2], off_desc, off_misc, off_par, off_w, off_tadj, total;
+};
+
+RecLayout make_rec_layout(const Layout& L, int max_iters, int every, int n_px, int num_sms) {
+    RecLayout R;
+    R.every = every;
+    R.max_iters = max_iters;
+    R.n_ckpt = (max_iters - 1) / every + 1;
+    R.slots = num_sms * kAdjSlotsPerSM;
+    const int need = (n_px + pv::ad::ADJ_THREADS - 1) / pv::ad::ADJ_THREADS * pv::ad::ADJ_THREADS;
+    if (need < R.slots) R.slots = need;
+    R.state_bytes = L.state_bytes;
+    R.adj_bytes = align_up((size_t)L.tiles_x * L.tiles_y * pv::TILE_WORDS * sizeof(double), kAlign);
+    size_t off = 0;
+    R.off_ckpt = off;
+    off += (size_t)R.n_ckpt * R.state_bytes;
+    R.off_seg = off;
+    off += (size_t)every * R.state_bytes;
+    for (int b = 0; b < 2; ++b) {
+        R.off_adj[b] = off;
+        off += R.adj_bytes;
+    }
+    R.off_desc = off;
+    off += align_up((size_t)max_iters * kDescBytes, kAlign);
+    R.off_misc = off;
+    off += kAlign;
+    const size_t nodes = (size_t)kTapeCap * R.slots;
+    R.off_par = off;
+    off += align_up(nodes * sizeof(int2), kAlign);
+    R.off_w = off;
+    off += align_up(nodes * sizeof(double2), kAlign);
+    R.off_tadj = off;
+    off += align_up(nodes * sizeof(double), kAlign);
+    R.total = off;
+    return R;
+}
+
 }  // namespace
 
 struct pixvod_handle {
@@ -107,6 +154,11 @@ struct pixvod_handle {
     int64_t frame_index;
     bool has_target;
     int64_t launches;
+    // recording for the adjoint
+    char* rec_ws;
+    RecLayout RL;
+    int rec_n;           // sweeps of the recorded frame (0: none)
+    bool rec_valid;      // the recorded frame can be differentiated
     // profiling
     bool profiling;
     std::vector<cudaEvent_t> ev;
@@ -255,6 +307,21 @@ pixvod_status run_sweeps(pixvod_handle* h, int n) {
     return PIXVOD_OK;
 }
 
+// the frame's sweeps with checkpoints for the adjoint: S_c before sweep c + 1
+// for c = 0, every, 2 every, ... (c < n)
+template <typename T>
+pixvod_status run_sweeps_recorded(pixvod_handle* h, int n) {
+    const RecLayout& R = h->RL;
+    for (int c = 0; c < n; c += R.every) {
+        pixvod_status s = cuda_status(cudaMemcpyAsync(h->rec_ws + R.off_ckpt + (size_t)(c / R.every) * R.state_bytes,
+                                                      h->ws + h->L.off_state[h->cur], R.state_bytes,
+                                                      cudaMemcpyDeviceToDevice, h->stream));
+        if (s != PIXVOD_OK) return s;
+        if ((s = run_sweeps<T>(h, n - c < R.every ? n - c : R.every)) != PIXVOD_OK) return s;
+    }
+    return PIXVOD_OK;
+}
+
 template <typename T>
 pixvod_status run_reduce(pixvod_handle* h, int anchor) {
     pv::k_reduce<T><<<h->L.tiles_x * h->L.tiles_y, pv::RED_THREADS, 0, h->stream>>>(
@@ -278,6 +345,7 @@ template <typename T>
 pixvod_status track_impl(pixvod_handle* h, const float* d_frame, const float* d_normals, int n_iters) {
     pixvod_status s;
     if (h->frame_index == 0) {
+        h->rec_valid = false;
         s = set_keyframe<T>(h, d_frame, d_normals);
         if (s != PIXVOD_OK) return s;
         h->frame_index = 1;
@@ -285,10 +353,18 @@ pixvod_status track_impl(pixvod_handle* h, const float* d_frame, const float* d_
         return PIXVOD_OK;
     }
     const bool kf = h->p.kf_interval > 0 && h->frame_index % h->p.kf_interval == 0;
+    if (h->rec_ws && n_iters > h->RL.max_iters) return PIXVOD_EINVAL;
+    h->rec_valid = false;
     pv::k_ingest_target<T><<<pixel_grid(h), pixel_block(), 0, h->stream>>>(
         geometry<T>(h), d_frame, input_ptr<T>(h, 1), input_ptr<T>(h, 2), input_ptr<T>(h, 3));
     if ((s = launched(h)) != PIXVOD_OK) return s;
-    if ((s = run_sweeps<T>(h, n_iters)) != PIXVOD_OK) return s;
+    if (h->rec_ws) {
+        if ((s = run_sweeps_recorded<T>(h, n_iters)) != PIXVOD_OK) return s;
+        h->rec_n = n_iters;
+        h->rec_valid = !kf;  // an anchoring frame replaces the state and the source image
+    } else if ((s = run_sweeps<T>(h, n_iters)) != PIXVOD_OK) {
+        return s;
+    }
     if ((s = run_reduce<T>(h, kf ? 1 : 0)) != PIXVOD_OK) return s;
     h->has_target = true;
     if (kf) {
@@ -297,6 +373,123 @@ pixvod_status track_impl(pixvod_handle* h, const float* d_frame, const float* d_
     }
     h->frame_index++;
     return PIXVOD_OK;
+}
+
+// Adjoint of the recorded frame's sweeps. The state after the sweeps seeds the
+// adjoint; each segment of `every` sweeps is recomputed from its checkpoint by
+// the sweep kernel, then differentiated sweep by sweep in reverse. Gradients are
+// truncated at the frame start (the carried state is a constant).
+template <typename T>
+pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* g_inv, double* g_sig, double* dIs,
+                            double* dIt, double* check) {
+    const RecLayout& R = h->RL;
+    const int n = h->rec_n, k = R.every;
+    const size_t npx = (size_t)h->K.width * h->K.height;
+    const int n_tiles = h->L.tiles_x * h->L.tiles_y;
+    cudaStream_t st = h->stream;
+    char* rw = h->rec_ws;
+    double* misc = reinterpret_cast<double*>(rw + R.off_misc);
+    double* dparam = misc;                                                        // 3 doubles
+    unsigned long long* mism = reinterpret_cast<unsigned long long*>(misc + 4);  // 1
+    unsigned* fl = reinterpret_cast<unsigned*>(misc + 5);                        // flags, max nodes
+    pixvod_status s = cuda_status(sweep_attributes<T>());
+    if (s == PIXVOD_OK) s = cuda_status(cudaMemsetAsync(dIs, 0, npx * sizeof(double), st));
+    if (s == PIXVOD_OK) s = cuda_status(cudaMemsetAsync(dIt, 0, npx * sizeof(double), st));
+    if (s == PIXVOD_OK) s = cuda_status(cudaMemsetAsync(misc, 0, kAlign, st));
+    if (s == PIXVOD_OK) s = cuda_status(cudaMemsetAsync(rw + R.off_adj[0], 0, R.adj_bytes, st));
+    if (s != PIXVOD_OK) return s;
+    double* adj[2] = {reinterpret_cast<double*>(rw + R.off_adj[0]), reinterpret_cast<double*>(rw + R.off_adj[1])};
+    auto ckpt = [&](int seg) { return reinterpret_cast<T*>(rw + R.off_ckpt + (size_t)seg * R.state_bytes); };
+    auto segbuf = [&](int j) { return reinterpret_cast<T*>(rw + R.off_seg + (size_t)(j - 1) * R.state_bytes); };
+    // descriptors of the recompute sweeps: sweep c + j maps S_{c+j-1} to S_{c+j}
+    std::vector<pv::SeqDesc<T>> descs(n > 0 ? n : 1);
+    const int n_seg = (n + k - 1) / k;
+    for (int seg = 0; seg < n_seg; ++seg)
+        for (int j = 1; j <= k && seg * k + j <= n; ++j) {
+            pv::SeqDesc<T> d = seq_desc<T>(h, nullptr, nullptr);
+            d.state[0] = j == 1 ? ckpt(seg) : segbuf(j - 1);
+            d.state[1] = segbuf(j);
+            descs[seg * k + j - 1] = d;
+        }
+    if (n > 0)
+        s = cuda_status(cudaMemcpyAsync(rw + R.off_desc, descs.data(), (size_t)n * sizeof(pv::SeqDesc<T>),
+                                        cudaMemcpyHostToDevice, st));
+    if (s != PIXVOD_OK) return s;
+    const pv::SeqDesc<T>* ddesc = reinterpret_cast<const pv::SeqDesc<T>*>(rw + R.off_desc);
+    pv::AdjArgs A;
+    A.g = geometry<double>(h);
+    A.state64 = h->p.precision == 64;
+    const Factors<double> F = factors<double>(h);
+    A.lam_D = F.lam_D;
+    A.inv_sigma_D = F.inv_sigma_D;
+    A.lam_N = F.lam_N;
+    A.lam_P = F.lam_P;
+    A.lam_Z = F.lam_Z;
+    A.lam_R = F.lam_R;
+    A.beta = F.beta;
+    A.t_huber = F.t_huber;
+    A.state_out = state_ptr<T>(h, h->cur);
+    h->launches++;
+    if ((s = cuda_status(pv::launch_adjoint_seed(A, g_xi, g_inv, adj[0], st))) != PIXVOD_OK) return s;
+    A.I_s = input_ptr<T>(h, 0);
+    A.I_t = input_ptr<T>(h, 1);
+    A.g_x = input_ptr<T>(h, 2);
+    A.g_y = input_ptr<T>(h, 3);
+    A.m_x = input_ptr<T>(h, 4);
+    A.m_y = input_ptr<T>(h, 5);
+    A.dI_s = dIs;
+    A.dI_t = dIt;
+    A.dparam = dparam;
+    A.mismatch = mism;
+    A.flags = fl;
+    A.max_nodes = fl + 1;
+    A.tape.par = reinterpret_cast<int2*>(rw + R.off_par);
+    A.tape.w = reinterpret_cast<double2*>(rw + R.off_w);
+    A.tape.adj = reinterpret_cast<double*>(rw + R.off_tadj);
+    A.tape.cap = kTapeCap;
+    A.tape.n_slots = R.slots;
+    // the prior mean of the segment the frame was tracked in
+    double d_prior = 0.0;
+    s = cuda_status(cudaMemcpyAsync(&d_prior, &scalars(h)->d_prior, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(st));
+    if (s != PIXVOD_OK) return s;
+    A.d_prior = d_prior;
+    int a = 0;  // adjoint buffer holding the adjoint of the later state
+    for (int seg = n_seg - 1; seg >= 0; --seg) {
+        const int c = seg * k, len = n - c < k ? n - c : k;
+        for (int j = 1; j <= len; ++j) {
+            pv::k_sweeps<T><<<n_tiles, sweep_block(), pv::sweep_smem_bytes<T>(), st>>>(
+                ddesc + (c + j - 1), nullptr, n_tiles, 1, 0, pv::GridSync{nullptr, nullptr, nullptr});
+            if ((s = launched(h)) != PIXVOD_OK) return s;
+        }
+        for (int j = len; j >= 1; --j) {
+            A.state_in = j == 1 ? ckpt(seg) : segbuf(j - 1);
+            A.state_out = segbuf(j);
+            A.adj_out = adj[a];
+            A.adj_in = adj[a ^ 1];
+            if ((s = cuda_status(cudaMemsetAsync(adj[a ^ 1], 0, R.adj_bytes, st))) != PIXVOD_OK) return s;
+            h->launches++;
+            if ((s = cuda_status(pv::launch_adjoint_sweep(A, R.slots / pv::ad::ADJ_THREADS, st))) != PIXVOD_OK)
+                return s;
+            a ^= 1;
+        }
+    }
+    h->launches++;
+    s = cuda_status(pv::launch_sigma_grads(dparam, double(h->p.sigma_D), double(h->p.sigma_N), g_sig, st));
+    if (s != PIXVOD_OK) return s;
+    unsigned long long mm = 0;
+    unsigned flags[2] = {0, 0};
+    s = cuda_status(cudaMemcpyAsync(&mm, mism, sizeof(mm), cudaMemcpyDeviceToHost, st));
+    if (s == PIXVOD_OK) s = cuda_status(cudaMemcpyAsync(flags, fl, sizeof(flags), cudaMemcpyDeviceToHost, st));
+    if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(st));
+    if (s != PIXVOD_OK) return s;
+    if (check) {
+        double m;
+        memcpy(&m, &mm, sizeof(m));
+        check[0] = m;
+        check[1] = double(flags[1]);
+    }
+    return (flags[0] & pv::FLAG_TAPE_FULL) ? PIXVOD_ENUMERIC : PIXVOD_OK;
 }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
@@ -402,6 +595,9 @@ pixvod_status pixvod_create(const pixvod_intrinsics* K, const pixvod_params* p, 
     h->prof_sweeps = 0;
     h->prof_ms = 0;
     h->prof_launch_base = 0;
+    h->rec_ws = nullptr;
+    h->rec_n = 0;
+    h->rec_valid = false;
     pixvod_status s = cuda_status(cudaMemsetAsync(h->ws, 0, L.total, h->stream));
     if (s == PIXVOD_OK) {
         // T_kf = T_cur = identity
@@ -622,6 +818,53 @@ pixvod_status pixvod_launch_count(pixvod_handle* h, int64_t* out) {
     if (!h || !out) return PIXVOD_EINVAL;
     *out = h->launches;
     return PIXVOD_OK;
+}
+
+static pixvod_status device_sms(int* sms) {
+    int dev = 0;
+    pixvod_status s = cuda_status(cudaGetDevice(&dev));
+    if (s == PIXVOD_OK) s = cuda_status(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev));
+    return s;
+}
+
+pixvod_status pixvod_backward_workspace_bytes(const pixvod_intrinsics* K, const pixvod_params* p, int32_t max_iters,
+                                              int32_t checkpoint_every, size_t* out_bytes) {
+    if (!intrinsics_ok(K) || !params_ok(p) || !out_bytes || max_iters < 1 || checkpoint_every < 1)
+        return PIXVOD_EINVAL;
+    int sms = 0;
+    pixvod_status s = device_sms(&sms);
+    if (s != PIXVOD_OK) return s;
+    *out_bytes = make_rec_layout(make_layout(K, p), max_iters, checkpoint_every, K->width * K->height, sms).total;
+    return PIXVOD_OK;
+}
+
+pixvod_status pixvod_set_recording(pixvod_handle* h, void* d_workspace, size_t ws_bytes, int32_t max_iters,
+                                   int32_t checkpoint_every) {
+    if (!h) return PIXVOD_EINVAL;
+    h->rec_valid = false;
+    h->rec_n = 0;
+    if (!d_workspace) {
+        h->rec_ws = nullptr;
+        return PIXVOD_OK;
+    }
+    if (!aligned(d_workspace, kAlign) || max_iters < 1 || checkpoint_every < 1) return PIXVOD_EINVAL;
+    int sms = 0;
+    pixvod_status s = device_sms(&sms);
+    if (s != PIXVOD_OK) return s;
+    RecLayout R = make_rec_layout(h->L, max_iters, checkpoint_every, h->K.width * h->K.height, sms);
+    if (ws_bytes < R.total) return PIXVOD_ENOMEM;
+    h->RL = R;
+    h->rec_ws = static_cast<char*>(d_workspace);
+    return PIXVOD_OK;
+}
+
+pixvod_status pixvod_backward(pixvod_handle* h, const double* d_grad_xi, const double* d_grad_invdepth,
+                              double* d_grad_sigmas, double* d_grad_Is, double* d_grad_It, double* check) {
+    if (!h || !d_grad_sigmas || !d_grad_Is || !d_grad_It) return PIXVOD_EINVAL;
+    if (!h->rec_ws || !h->rec_valid) return PIXVOD_ESTATE;
+    return h->p.precision == 64
+               ? backward_impl<double>(h, d_grad_xi, d_grad_invdepth, d_grad_sigmas, d_grad_Is, d_grad_It, check)
+               : backward_impl<float>(h, d_grad_xi, d_grad_invdepth, d_grad_sigmas, d_grad_Is, d_grad_It, check);
 }
 
 }  // extern "C"
@@ -896,6 +1139,9 @@ pixvod_status pixvod_batch_create(int32_t n, const pixvod_intrinsics* K, const p
         h.prof_sweeps = 0;
         h.prof_ms = 0;
         h.prof_launch_base = 0;
+        h.rec_ws = nullptr;
+        h.rec_n = 0;
+        h.rec_valid = false;
     }
     int dev = 0;
     s = cuda_status(cudaGetDevice(&dev));

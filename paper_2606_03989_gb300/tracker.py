@@ -160,6 +160,85 @@ class Tracker:
         nat.check(nat.lib.pixvod_launch_count(self._h, ctypes.byref(n)), "pixvod_launch_count")
         return n.value
 
+    # --- adjoint ---------------------------------------------------------
+    def set_recording(self, max_iters: int, checkpoint_every: int = 5):
+        """Record target frames (up to max_iters sweeps) for backward()."""
+        torch = self._torch
+        need = ctypes.c_size_t(0)
+        nat.check(nat.lib.pixvod_backward_workspace_bytes(ctypes.byref(self.K), ctypes.byref(self.params),
+                                                          int(max_iters), int(checkpoint_every), ctypes.byref(need)),
+                  "pixvod_backward_workspace_bytes")
+        self._rec = torch.empty(need.value + 256, dtype=torch.uint8, device=self.device)
+        ptr = (self._rec.data_ptr() + 255) // 256 * 256
+        nat.check(nat.lib.pixvod_set_recording(self._h, ptr, need.value, int(max_iters), int(checkpoint_every)),
+                  "pixvod_set_recording")
+
+    def stop_recording(self):
+        nat.check(nat.lib.pixvod_set_recording(self._h, None, 0, 1, 1), "pixvod_set_recording")
+        self._rec = None
+
+    def backward(self, grad_xi=None, grad_invdepth=None) -> dict:
+        """Gradients of a loss through the last recorded frame's sweeps, given
+        dL/dxi_est (6) and dL/d(inverse depth) (H, W); FP64 CUDA tensors out."""
+        torch = self._torch
+        H, W = self.shape
+        f64 = dict(dtype=torch.float64, device=self.device)
+        gx = None if grad_xi is None else torch.as_tensor(grad_xi).to(**f64).reshape(6).contiguous()
+        gi = None if grad_invdepth is None else torch.as_tensor(grad_invdepth).to(**f64).reshape(H, W).contiguous()
+        g_sig = torch.empty(2, **f64)
+        g_Is = torch.empty(H, W, **f64)
+        g_It = torch.empty(H, W, **f64)
+        check = (ctypes.c_double * 2)()
+        nat.check(nat.lib.pixvod_backward(self._h, _ptr(gx), _ptr(gi), g_sig.data_ptr(), g_Is.data_ptr(),
+                                          g_It.data_ptr(), ctypes.cast(check, ctypes.c_void_p)), "pixvod_backward")
+        return {"sigma_D": g_sig[0], "sigma_N": g_sig[1], "I_s": g_Is, "I_t": g_It,
+                "recompute_mismatch": check[0], "tape_nodes": int(check[1])}
+
+
+def _track_frame_function():
+    import torch
+
+    class TrackFrame(torch.autograd.Function):
+        """One recorded target frame as a differentiable function of the keyframe
+        image, the target frame and the photometric / normal-prior sigmas."""
+
+        @staticmethod
+        def forward(ctx, trk, n_iters, keyframe, frame, sigma_D, sigma_N):
+            for name, t in (("sigma_D", sigma_D), ("sigma_N", sigma_N)):
+                if abs(float(t) - getattr(trk.params, name)) > 1e-6 * abs(float(t)):
+                    raise ValueError("%s must equal the tracker's parameter" % name)
+            trk.track(frame.detach().contiguous(), None, n_iters)
+            xi = trk.pose_device().clone()
+            inv = trk.inv_depth().to(torch.float64)
+            ctx.trk = trk
+            ctx.dtypes = (keyframe.dtype, frame.dtype, sigma_D.dtype, sigma_N.dtype)
+            return xi, inv
+
+        @staticmethod
+        def backward(ctx, g_xi, g_inv):
+            g = ctx.trk.backward(g_xi, g_inv)
+            dk, df, ds, dn = ctx.dtypes
+            return (None, None, g["I_s"].to(dk), g["I_t"].to(df), g["sigma_D"].to(ds).reshape(()),
+                    g["sigma_N"].to(dn).reshape(()))
+
+    return TrackFrame
+
+
+_TrackFrame = None
+
+
+def track_frame(trk: Tracker, frame, keyframe, sigma_D, sigma_N, n_iters: int = 20):
+    """Track `frame` (a target frame) with recording on and return (xi_est,
+    inverse depth) as autograd outputs of (keyframe, frame, sigma_D, sigma_N).
+    `keyframe` must be the image the tracker holds as its keyframe, and the
+    sigmas (0-dim tensors) its parameters; gradients flow to all four."""
+    global _TrackFrame
+    if _TrackFrame is None:
+        _TrackFrame = _track_frame_function()
+    if getattr(trk, "_rec", None) is None:
+        trk.set_recording(max(int(n_iters), 1))
+    return _TrackFrame.apply(trk, int(n_iters), keyframe, frame, sigma_D, sigma_N)
+
 
 class Batch:
     """Many sequences (own intrinsics and state, shared params) advanced together.

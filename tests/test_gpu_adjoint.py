@@ -1,0 +1,196 @@
+"""Adjoint of the unrolled sweeps of one frame (pixvod_backward) against central
+finite differences of the FP64 oracle: gradients of
+    L = |xi_est - xi_gt|^2 + mean_px (exp(-mu_6) - 1/z_gt)^2
+with respect to sigma_D, sigma_N and the keyframe / target intensities, for a
+16 x 12 realistic pair tracked with 5 sweeps (checkpoints every 2 sweeps, so
+the recompute runs segments of 2, 2 and 1 sweeps). Tolerance: relative error
+1e-3, the bound the derivative is specified to.
+
+The iteration is very sensitive (the loss moves by ~4e3 relative per relative
+change of sigma_D but ~0.07 per relative change of sigma_N), so no single
+difference step suits every input: small steps drown in the rounding noise of
+the FP64 trajectory, large ones in its curvature. Each finite difference is
+therefore taken over a ladder of steps, and the value used is the best-agreeing
+adjacent pair (the plateau), which must itself agree to 2e-3."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import synth  # noqa: E402
+import paper_2606_03989_gb300 as pv  # noqa: E402
+from oracle import gbp, lie  # noqa: E402
+from oracle import tracker as otr  # noqa: E402
+from helpers import f32, oracle_intrinsics  # noqa: E402
+
+DEV = torch.device("cuda:0")
+W, H, SWEEPS, EVERY = 16, 12, 5, 2
+RTOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def case():
+    seq = synth.realistic(5, 2, W, H)
+    T = seq.relative_pose(0, 1)
+    xi_gt = lie.se3_log(T[:3, :3], T[:3, 3])
+    inv_gt = 1.0 / seq.depth(0)
+    return {"seq": seq, "I_s": seq.frame(0), "I_t": seq.frame(1), "n": seq.normals(0),
+            "xi_gt": xi_gt, "inv_gt": inv_gt}
+
+
+def loss(c, xi, inv):
+    return float(np.sum((xi - c["xi_gt"]) ** 2) + np.mean((inv - c["inv_gt"]) ** 2))
+
+
+def oracle_params(seq, sigma_D=None, sigma_N=None):
+    """The GPU's float32 parameters; sigma_D / sigma_N may be given unrounded."""
+    p = pv.params_default()
+    return gbp.Params(sigma_D=f32(p.sigma_D) if sigma_D is None else sigma_D, sigma_P=f32(seq.sigma_P),
+                      sigma_R=f32(p.sigma_R), sigma_N=f32(p.sigma_N) if sigma_N is None else sigma_N,
+                      sigma_Z=f32(p.sigma_Z), t_huber=f32(p.t_huber), damping=f32(p.damping))
+
+
+def oracle_loss(c, I_s=None, I_t=None, **sig):
+    seq = c["seq"]
+    trk = otr.Tracker(oracle_intrinsics(seq.cam), oracle_params(seq, **sig), kf_interval=0)
+    trk.track(np.asarray(c["I_s"] if I_s is None else I_s, np.float64), c["n"])
+    xi = trk.track(np.asarray(c["I_t"] if I_t is None else I_t, np.float64), n_iters=SWEEPS)
+    return loss(c, xi, np.exp(-trk.state.mu[..., 6]))
+
+
+def gpu_run(c, precision=64):
+    seq = c["seq"]
+    trk = pv.Tracker(seq.cam.as_tuple(), pv.params(precision=precision, kf_interval=0, sigma_P=seq.sigma_P), DEV)
+    trk.set_recording(SWEEPS, EVERY)
+    trk.track(torch.from_numpy(c["I_s"]).to(DEV), torch.from_numpy(c["n"]).to(DEV))
+    trk.track(torch.from_numpy(c["I_t"]).to(DEV), n_iters=SWEEPS)
+    xi = trk.pose()
+    inv = np.exp(-trk.state().mu[..., 6])   # the mean in the state's own precision
+    g = trk.backward(2.0 * (xi - c["xi_gt"]), 2.0 * (inv - c["inv_gt"]) / inv.size)
+    return trk, xi, inv, g
+
+
+@pytest.fixture(scope="module")
+def gpu64(case):
+    return gpu_run(case, 64)
+
+
+def central(f, x0, h):
+    return (f(x0 + h) - f(x0 - h)) / (2.0 * h)
+
+
+STEPS = [3e-3, 1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7, 1e-7]
+
+
+def plateau(f, x0, unit):
+    """Central differences of f at x0 over steps unit * STEPS; the mean of the
+    adjacent pair that agrees best, which must agree to 2e-3."""
+    d = [central(f, x0, unit * h) for h in STEPS]
+    spread = [abs(a - b) / max(abs(a), abs(b), 1e-300) for a, b in zip(d, d[1:])]
+    k = int(np.argmin(spread))
+    assert spread[k] <= 2e-3, (d, spread)
+    return 0.5 * (d[k] + d[k + 1])
+
+
+def assert_close(g, fd, scale):
+    assert abs(g - fd) <= RTOL * max(abs(fd), scale), (g, fd, scale)
+
+
+def test_recomputed_update_equals_the_sweep_kernel(gpu64):
+    """The derivative's own FP64 recomputation of every pixel update matches the
+    sweep kernel's result, so the tape differentiates the function that ran."""
+    _, _, _, g = gpu64
+    assert g["recompute_mismatch"] < 1e-9, g["recompute_mismatch"]
+    assert 1000 < g["tape_nodes"] < 16384
+
+
+def test_loss_matches_the_oracle(case, gpu64):
+    _, xi, inv, _ = gpu64
+    assert loss(case, xi, inv) == pytest.approx(oracle_loss(case), rel=1e-9)
+
+
+def test_sigma_gradients_match_oracle_finite_differences(case, gpu64):
+    _, _, _, g = gpu64
+    p = pv.params_default()
+    sD, sN = f32(p.sigma_D), f32(p.sigma_N)
+    fd_D = plateau(lambda s: oracle_loss(case, sigma_D=s), sD, sD)
+    fd_N = plateau(lambda s: oracle_loss(case, sigma_N=s), sN, sN)
+    assert fd_D != 0.0 and fd_N != 0.0
+    assert_close(float(g["sigma_D"]), fd_D, 0.0)
+    assert_close(float(g["sigma_N"]), fd_N, 0.0)
+
+
+def test_intensity_gradients_match_oracle_finite_differences(case, gpu64):
+    _, _, _, g = gpu64
+    rng = np.random.default_rng(11)
+    pix = [(int(rng.integers(1, H - 1)), int(rng.integers(1, W - 1))) for _ in range(3)]
+    for name in ("I_s", "I_t"):
+        gg = g[name].cpu().numpy()
+        fds = []
+        for (v, u) in pix:
+            def f(x, v=v, u=u):
+                img = case[name].astype(np.float64).copy()
+                img[v, u] = x
+                return oracle_loss(case, **{name: img})
+            fds.append(plateau(f, float(case[name][v, u]), 1.0))
+        scale = 1e-2 * max(abs(x) for x in fds)
+        assert scale > 0.0
+        for (v, u), fd in zip(pix, fds):
+            assert_close(float(gg[v, u]), fd, scale)
+
+
+def test_autograd_function_gives_the_backward_gradients(case, gpu64):
+    seq = case["seq"]
+    trk = pv.Tracker(seq.cam.as_tuple(), pv.params(precision=64, kf_interval=0, sigma_P=seq.sigma_P), DEV)
+    kf = torch.from_numpy(case["I_s"]).to(DEV).requires_grad_(True)
+    fr = torch.from_numpy(case["I_t"]).to(DEV).requires_grad_(True)
+    p = pv.params_default()
+    sD = torch.tensor(f32(p.sigma_D), dtype=torch.float64, requires_grad=True)
+    sN = torch.tensor(f32(p.sigma_N), dtype=torch.float64, requires_grad=True)
+    trk.set_recording(SWEEPS, EVERY)
+    trk.track(kf.detach(), torch.from_numpy(case["n"]).to(DEV))
+    xi, inv = pv.track_frame(trk, fr, kf, sD, sN, SWEEPS)
+    xi_gt = torch.as_tensor(case["xi_gt"], device=DEV)
+    inv_gt = torch.as_tensor(case["inv_gt"], device=DEV)
+    L = ((xi - xi_gt) ** 2).sum() + ((inv - inv_gt) ** 2).mean()
+    L.backward()
+    _, _, _, g = gpu64
+    assert float(L) == pytest.approx(loss(case, *gpu64[1:3]), rel=1e-6)
+    assert float(sD.grad) == pytest.approx(float(g["sigma_D"]), rel=1e-5)
+    assert float(sN.grad) == pytest.approx(float(g["sigma_N"]), rel=1e-5)
+    assert torch.allclose(kf.grad.double(), g["I_s"], rtol=1e-5, atol=1e-9 * float(g["I_s"].abs().max()))
+    assert torch.allclose(fr.grad.double(), g["I_t"], rtol=1e-5, atol=1e-9 * float(g["I_t"].abs().max()))
+
+
+def test_fp32_state_gives_close_gradients(case, gpu64):
+    _, _, _, g64 = gpu64
+    _, _, _, g32 = gpu_run(case, 32)
+    # one FP32 sweep against its FP64 recomputation (relative to max(1, |value|))
+    assert g32["recompute_mismatch"] < 1e-2
+    for k in ("sigma_D", "sigma_N"):
+        assert np.isfinite(float(g32[k]))
+        assert float(g32[k]) == pytest.approx(float(g64[k]), rel=0.1)
+
+
+def test_backward_needs_a_recorded_frame(case):
+    seq = case["seq"]
+    trk = pv.Tracker(seq.cam.as_tuple(), pv.params(precision=64, kf_interval=2, sigma_P=seq.sigma_P), DEV)
+    lib = pv.lib
+    z = torch.zeros(H * W + 8, dtype=torch.float64, device=DEV)
+    args = (None, None, z.data_ptr(), z.data_ptr(), z.data_ptr(), None)
+    assert lib.pixvod_backward(trk._h, *args) == pv.ESTATE  # recording off
+    trk.set_recording(SWEEPS, EVERY)
+    I_s = torch.from_numpy(case["I_s"]).to(DEV)
+    n = torch.from_numpy(case["n"]).to(DEV)
+    trk.track(I_s, n)
+    assert lib.pixvod_backward(trk._h, *args) == pv.ESTATE  # a keyframe, not a target
+    with pytest.raises(pv.PixvodError):
+        trk.track(torch.from_numpy(case["I_t"]).to(DEV), n_iters=SWEEPS + 1)  # more sweeps than recorded
+    trk.track(torch.from_numpy(case["I_t"]).to(DEV), n_iters=SWEEPS)  # frame 1: a target
+    assert lib.pixvod_backward(trk._h, *args) == pv.OK
+    trk.track(I_s, n, n_iters=SWEEPS)  # frame 2 anchors a new keyframe
+    assert lib.pixvod_backward(trk._h, *args) == pv.ESTATE
