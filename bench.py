@@ -57,6 +57,13 @@ def _render_batched(args):
     return idx, k, seq.frame(k), seq.normals(k)
 
 
+def _render_adjoint(args):
+    idx, k, n_frames = args
+    import synth
+    seq = synth.adjoint_family(8, n_frames)[idx]
+    return idx, k, seq.frame(k), seq.normals(k) if k == 0 else None, seq.depth(0) if k == 0 else None
+
+
 def render_frames(seed, n_frames, kf_interval, procs):
     """Frames 0..n_frames-1 (normals for keyframes), rendered by a spawn pool."""
     import multiprocessing as mp
@@ -418,6 +425,111 @@ def run_batched(args):
     return 0
 
 
+def run_adjoint(args):
+    """Adjoint workload: 8 sequences of the realistic family at 320x240 (fx=fy=262.5),
+    30 sweeps per frame, checkpoints every 5 sweeps. One step = every sequence
+    tracks one frame (FP32 state, recording on) and back-propagates the frame's
+    loss |xi_est - xi_gt|^2 + mean_px (exp(-mu_6) - 1/z_gt)^2 through its sweeps
+    (FP64 adjoint), giving dL/dsigma_D, dL/dsigma_N, dL/dI_s and dL/dI_t. The same
+    frames are also tracked without recording or backward, for the ratio."""
+    import multiprocessing as mp
+    import synth
+    import torch
+    import paper_2606_03989_gb300 as pv
+    sys.path.insert(0, ROOT)
+    n_seq, sweeps, every = 8, 30, 5
+    n_frames = 1 + args.warmup + args.steps
+    fam = synth.adjoint_family(n_seq, n_frames)
+    jobs = [(i, k, n_frames) for i in range(n_seq) for k in range(n_frames)]
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 2))) as pool:
+        rendered = pool.map(_render_adjoint, jobs)
+    dev = torch.device("cuda", 0)
+    frames = [[None] * n_frames for _ in range(n_seq)]
+    normals, inv_gt = [None] * n_seq, [None] * n_seq
+    for i, k, f, n, z in rendered:
+        frames[i][k] = torch.from_numpy(f).to(dev)
+        if k == 0:
+            normals[i] = torch.from_numpy(n).to(dev)
+            inv_gt[i] = torch.from_numpy(1.0 / z).to(dev)
+    xi_gt = [[_se3_log(q.relative_pose(0, k)) for k in range(n_frames)] for q in fam]
+    px = sum(q.cam.width * q.cam.height for q in fam)
+    params = pv.params(precision=32, kf_interval=0, sigma_P=fam[0].sigma_P)
+    stream = torch.cuda.Stream(dev)
+    out = {}
+    for mode in ("forward", "backward"):
+        with torch.cuda.stream(stream):
+            trks = [pv.Tracker(q.cam.as_tuple(), params, dev, stream=stream) for q in fam]
+            if mode == "backward":
+                for t in trks:
+                    t.set_recording(sweeps, every)
+            for i, t in enumerate(trks):
+                t.track(frames[i][0], normals[i])
+            grads, checks = [], []
+            stream.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t_host = 0.0
+            for k in range(1, n_frames):
+                if k == 1 + args.warmup:
+                    ev0.record(stream)
+                    t_host = time.perf_counter()
+                for i, t in enumerate(trks):
+                    t.track(frames[i][k], None, sweeps)
+                    if mode == "backward":
+                        xi = t.pose_device()
+                        inv = t.inv_depth().double()
+                        gx = 2.0 * (xi - torch.as_tensor(xi_gt[i][k], device=dev))
+                        gi = 2.0 * (inv - inv_gt[i]) / inv.numel()
+                        g = t.backward(gx, gi)
+                        if k == n_frames - 1:
+                            grads.append(g)
+            ev1.record(stream)
+            ev1.synchronize()
+            out[mode] = {"ms": ev0.elapsed_time(ev1), "host_s": time.perf_counter() - t_host,
+                         "launches": sum(t.launch_count() for t in trks),
+                         "flags": int(np.bitwise_or.reduce([t.status() for t in trks]))}
+            if mode == "backward":
+                out["grads"] = grads
+            del trks
+    fb, fw = out["backward"]["ms"], out["forward"]["ms"]
+    g = out["grads"]
+    line = {
+        "metric": "adjoint: Mpixel*GBP-sweeps/s differentiated (forward + backward), 8 x 320x240",
+        "value": px * sweeps * args.steps / (fb * 1e-3) / 1e6, "unit": "Mpx*sweeps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": fb / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, f64 adjoint", "data": "synthetic",
+        "config": {"workload": "adjoint: 8 sequences of the realistic family (seeds 2000-2007) at 320x240, "
+                               "fx=fy=262.5, %d sweeps per frame, checkpoint every %d sweeps, loss per frame "
+                               "truncated at the frame start" % (sweeps, every),
+                   "pixels_per_step": px},
+        "forward_only": {"value": px * sweeps * args.steps / (fw * 1e-3) / 1e6, "ms_per_step": fw / args.steps},
+        "time_ratio_fwd_bwd_over_fwd": fb / fw,
+        "last_step_grads": {"sigma_D": [float(x["sigma_D"]) for x in g], "sigma_N": [float(x["sigma_N"]) for x in g],
+                            "recompute_mismatch_max": max(x["recompute_mismatch"] for x in g),
+                            "tape_nodes_max": max(x["tape_nodes"] for x in g)},
+        "device_flags": out["backward"]["flags"] | out["forward"]["flags"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _se3_log(T):
+    """[theta; rho] of a 4x4 rigid transform (plain numpy: host-side target poses)."""
+    R, t = T[:3, :3], T[:3, 3]
+    c = np.clip(0.5 * (np.trace(R) - 1.0), -1.0, 1.0)
+    th = float(np.arccos(c))
+    w = 0.5 * np.array([R[2, 1] - R[1, 2], R[0, 2] - R[2, 0], R[1, 0] - R[0, 1]])
+    A = np.sin(th) / th if th > 1e-8 else 1.0 - th * th / 6.0
+    theta = w / A
+    W_ = np.array([[0, -theta[2], theta[1]], [theta[2], 0, -theta[0]], [-theta[1], theta[0], 0]])
+    if th > 1e-8:
+        B = (1 - np.cos(th)) / th ** 2
+        D = (1 - A / (2 * B)) / th ** 2
+    else:
+        D = 1.0 / 12.0
+    Vinv = np.eye(3) - 0.5 * W_ + D * (W_ @ W_)
+    return np.concatenate([theta, Vinv @ t])
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,7 +537,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--sweeps", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="realistic", choices=["realistic", "batched"])
+    ap.add_argument("--workload", default="realistic", choices=["realistic", "batched", "adjoint"])
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -435,6 +547,8 @@ def main(argv=None):
     build.build()
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_gpu(args)
 
 

@@ -100,8 +100,8 @@ Layout make_layout(const pixvod_intrinsics* K, const pixvod_params* p) {
 // every `every` sweeps, the states of one segment recomputed from a checkpoint,
 // two adjoint states (FP64), descriptors of the recompute launches, the
 // reverse-mode tapes of the adjoint kernel and a few accumulators.
-constexpr int kTapeCap = 16384;           // tape nodes per thread
-constexpr int kAdjSlotsPerSM = 32;        // adjoint threads per SM (one block)
+constexpr int kTapeCap = 9216;            // tape nodes per thread (about 7200 used)
+constexpr int kAdjSlotsPerSM = 128;       // adjoint threads per SM (four blocks)
 struct RecLayout {
     int n_ckpt, every, max_iters, slots;
     size_t state_bytes, adj_bytes;
