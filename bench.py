@@ -64,6 +64,14 @@ def _render_adjoint(args):
     return idx, k, seq.frame(k), seq.normals(k) if k == 0 else None, seq.depth(0) if k == 0 else None
 
 
+def _render_ablation(args):
+    seed, k, n_frames = args
+    import synth
+    seq = synth.realistic(seed, n_frames, 320, 240, f=262.5)
+    clean = seq.clean(k)
+    return k, clean["image"].astype(np.float64), seq.frame(k), clean["normal"].astype(np.float32)
+
+
 def render_frames(seed, n_frames, kf_interval, procs):
     """Frames 0..n_frames-1 (normals for keyframes), rendered by a spawn pool."""
     import multiprocessing as mp
@@ -512,6 +520,105 @@ def run_adjoint(args):
     return 0
 
 
+def _pose_errors(T_est, T_gt):
+    """(rotation error in degrees, translation error in metres) of a 4x4 estimate."""
+    R = T_est[:3, :3].T @ T_gt[:3, :3]
+    ang = float(np.degrees(np.arccos(np.clip(0.5 * (np.trace(R) - 1.0), -1.0, 1.0))))
+    return ang, float(np.linalg.norm(T_est[:3, 3] - T_gt[:3, 3]))
+
+
+def _translation_shape(T_est, T_gt):
+    """(angle in degrees between estimated and true translation, |t_est| / |t_gt|)."""
+    a, b = T_est[:3, 3], T_gt[:3, 3]
+    na, nb = np.linalg.norm(a), np.linalg.norm(b)
+    if na == 0.0 or nb == 0.0:
+        return float("nan"), float(na / nb) if nb else float("nan")
+    return float(np.degrees(np.arccos(np.clip(a @ b / (na * nb), -1.0, 1.0)))), float(na / nb)
+
+
+def _set_keyframe_depth(trk, depth):
+    """Replace the keyframe reset's log-depth (and the log-depth prior mean) by
+    log(depth), through the checkpoint API (header and plane layout of
+    include/pixvod.h; d_prior is scalar 38)."""
+    blob = bytearray(trk.save_state())
+    hd = np.frombuffer(bytes(blob[:96]), dtype="<i8")
+    prec, W, H, pitch, off_p, off_s = (int(hd[i]) for i in (2, 3, 4, 5, 8, 9))
+    dt = np.float32 if prec == 32 else np.float64
+    elt = np.dtype(dt).itemsize
+    plane = np.frombuffer(blob, dtype=dt, count=H * pitch, offset=off_p + 6 * H * pitch * elt).reshape(H, pitch)
+    logz = np.log(depth)
+    plane[:, :W] = logz
+    sc = np.frombuffer(blob, dtype=np.float64, count=40, offset=off_s)
+    sc[38] = float(logz.mean())
+    trk.load_state(bytes(blob))
+
+
+def run_ablation(args):
+    """Accuracy curves on a synthetic sequence (the paper's Replica experiments are
+    not reproducible here): pose error against ground truth for several numbers of
+    sweeps per frame, for the sequence's own noise and the App. D.1 sensor model
+    (mild, strong), and the basin of convergence: keyframe 0 against each of the next
+    12 frames from a reset (log-depth 0, or the ground-truth depth), final error
+    against initial error. 320x240 realistic sequence (seed 2000, fx=fy=262.5), 31
+    frames, keyframe every 10 frames."""
+    import multiprocessing as mp
+    import synth
+    import torch
+    import paper_2606_03989_gb300 as pv
+    seed, n_frames, kf = 2000, 31, 10
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 2))) as pool:
+        rendered = pool.map(_render_ablation, [(seed, k, n_frames) for k in range(n_frames)])
+    rendered.sort(key=lambda r: r[0])
+    seq = synth.realistic(seed, n_frames, 320, 240, f=262.5)
+    dev = torch.device("cuda", 0)
+    frames = {"default": [r[2] for r in rendered]}
+    for name, th in (("mild", synth.THETA_MILD), ("strong", synth.THETA_STRONG)):
+        frames[name] = [synth.ppa_noise(r[1], th, np.random.default_rng([seed, r[0], 99])) for r in rendered]
+    normals = [torch.from_numpy(r[3]).to(dev) for r in rendered]
+    gt = [seq.relative_pose(0, k) for k in range(n_frames)]
+    params = pv.params(precision=32, kf_interval=kf, sigma_P=seq.sigma_P)
+
+    def track_all(imgs, sweeps):
+        trk = pv.Tracker(seq.cam.as_tuple(), params, dev)
+        rot, tr = [], []
+        for k in range(n_frames):
+            trk.track(torch.from_numpy(imgs[k]).to(dev), normals[k] if k % kf == 0 else None, sweeps)
+            if k > 0:
+                e = _pose_errors(trk.pose_global(), gt[k])
+                rot.append(e[0])
+                tr.append(e[1])
+        return {"rot_deg_mean": float(np.mean(rot)), "rot_deg_last": rot[-1],
+                "trans_cm_mean": 100 * float(np.mean(tr)), "trans_cm_last": 100 * tr[-1], "flags": trk.status()}
+
+    curves = {name: {str(sw): track_all(frames[name], sw) for sw in (5, 10, 20, 40)} for name in frames}
+    basin = {"reset_depth": [], "gt_depth": []}
+    for init in basin:
+        for k in range(1, 13):
+            trk = pv.Tracker(seq.cam.as_tuple(), params, dev)
+            trk.track(torch.from_numpy(frames["default"][0]).to(dev), normals[0])
+            if init == "gt_depth":
+                _set_keyframe_depth(trk, seq.depth(0))
+            trk.track(torch.from_numpy(frames["default"][k]).to(dev), None, 20)
+            r0, t0 = _pose_errors(np.eye(4), gt[k])
+            T = trk.pose_global()
+            r1, t1 = _pose_errors(T, gt[k])
+            dirn, scale = _translation_shape(T, gt[k])
+            basin[init].append({"frames_apart": k, "init_rot_deg": r0, "init_trans_cm": 100 * t0,
+                                "final_rot_deg": r1, "final_trans_cm": 100 * t1,
+                                "trans_dir_err_deg": dirn, "trans_scale": scale, "flags": trk.status()})
+    line = {
+        "metric": "mean translation error over the sequence, 20 sweeps per frame, sequence noise",
+        "value": curves["default"]["20"]["trans_cm_mean"], "unit": "cm", "n_gpus": 1, "higher_is_better": False,
+        "data": "synthetic", "dtype": "f32",
+        "config": {"workload": "ablation: realistic 320x240 (seed 2000, fx=fy=262.5), %d frames, keyframe every %d; "
+                               "noise: sequence default (2/255, 8 bit, 1%% dropout), App. D.1 mild / strong"
+                               % (n_frames, kf)},
+        "sweeps_and_noise": curves, "basin_20_sweeps": basin,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _se3_log(T):
     """[theta; rho] of a 4x4 rigid transform (plain numpy: host-side target poses)."""
     R, t = T[:3, :3], T[:3, 3]
@@ -537,7 +644,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--sweeps", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="realistic", choices=["realistic", "batched", "adjoint"])
+    ap.add_argument("--workload", default="realistic", choices=["realistic", "batched", "adjoint", "ablation"])
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -549,6 +656,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "ablation":
+        return run_ablation(args)
     return run_gpu(args)
 
 
