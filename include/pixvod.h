@@ -83,8 +83,25 @@ typedef struct {
     float damping;     /* beta in m <- (1 - beta) m_new + beta m_old, in [0, 1) */
     int32_t kf_interval; /* frame k > 0 with k % kf_interval == 0 becomes a keyframe; 0 = never */
     int32_t precision;   /* arithmetic and state precision: 32 (float) or 64 (double) */
-    int32_t reserved[7]; /* must be zero */
+    int32_t topology;    /* identity factors: PIXVOD_TOPOLOGY_GRID (0, default) or _QUADTREE (1) */
+    int32_t reserved[6]; /* must be zero */
 } pixvod_params;
+
+/* Camera-motion identity factor patterns (Eq. 5).
+ * GRID: between every pair of horizontally or vertically adjacent pixels.
+ * QUADTREE: the hierarchical pattern of the paper's main experiments (Sec. 3.3
+ *   factor graph): a pose node per 2x2 block of pixels (level 1), per 2x2 block
+ *   of level-1 nodes (level 2), ... up to one root; each pixel or node is joined
+ *   to its parent only, the factor between levels l - 1 and l with sigma_R / 2^(l-1),
+ *   and a level-l node carries a pose prior with sigma_P / 2^l (Sec. 4.2: both
+ *   halved per level). An image of w x h has ceil(w / 2^l) x ceil(h / 2^l) nodes at
+ *   level l. The normal-integration factors stay on the pixel grid. A quadtree
+ *   handle stores its pixel state in the same layout (identity slot 0 holds the
+ *   message from the parent, slots 1..3 are zero); the node states are not in
+ *   checkpoints, so pixvod_load_state and the adjoint (pixvod_set_recording) return
+ *   ESTATE, and batches take grid handles only. */
+#define PIXVOD_TOPOLOGY_GRID 0
+#define PIXVOD_TOPOLOGY_QUADTREE 1
 
 typedef struct pixvod_handle pixvod_handle;
 
@@ -115,7 +132,7 @@ size_t pixvod_state_bytes_per_pixel(int32_t precision);
  * stream). Enqueues a memset of the workspace. EINVAL on null or misaligned
  * workspace, invalid intrinsics (fx, fy <= 0, width or height < 2) or params
  * (any sigma <= 0, damping outside [0, 1), precision not 32/64, nonzero
- * reserved); ENOMEM if ws_bytes is too small. */
+ * reserved, topology not 0/1); ENOMEM if ws_bytes is too small. */
 pixvod_status pixvod_create(const pixvod_intrinsics* K, const pixvod_params* p, void* d_workspace,
                             size_t ws_bytes, void* stream, pixvod_handle** out);
 

@@ -10,6 +10,7 @@ import importlib
 
 _NATIVE = {"ECUDA", "EINVAL", "ENOMEM", "ENUMERIC", "ESTATE", "ETIMEOUT", "FLAG_NONFINITE",
            "SCHED_PLAIN", "SCHED_BATCHED", "SCHED_PERSISTENT", "SCHED_NAMES",
+           "TOPOLOGY_GRID", "TOPOLOGY_QUADTREE", "pixvod_intrinsics",
            "FLAG_NONPOS_PIVOT", "FLAG_TIMEOUT", "LIB_PATH", "OK", "PixvodError", "StateView",
            "intrinsics", "lib", "params", "params_default", "parse_state", "status_string",
            "workspace_bytes"}

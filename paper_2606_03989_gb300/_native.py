@@ -16,6 +16,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "lib", "libpixvod.so")
 
 OK, EINVAL, ECUDA, ENUMERIC, ESTATE, ETIMEOUT, ENOMEM = range(7)
+TOPOLOGY_GRID, TOPOLOGY_QUADTREE = 0, 1
 SCHED_PLAIN, SCHED_BATCHED, SCHED_PERSISTENT = 0, 1, 2
 SCHED_NAMES = {SCHED_PLAIN: "plain", SCHED_BATCHED: "batched", SCHED_PERSISTENT: "persistent"}
 FLAG_NONPOS_PIVOT, FLAG_NONFINITE, FLAG_TIMEOUT = 0x1, 0x2, 0x4
@@ -39,7 +40,8 @@ class pixvod_params(ctypes.Structure):
     _fields_ = [("sigma_D", ctypes.c_float), ("sigma_P", ctypes.c_float), ("sigma_R", ctypes.c_float),
                 ("sigma_N", ctypes.c_float), ("sigma_Z", ctypes.c_float), ("t_huber", ctypes.c_float),
                 ("damping", ctypes.c_float), ("kf_interval", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("precision", ctypes.c_int32), ("topology", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class pixvod_profile(ctypes.Structure):

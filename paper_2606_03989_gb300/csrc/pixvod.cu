@@ -13,6 +13,7 @@
 #include "../../include/pixvod.h"
 #include "pv_adjoint_api.h"
 #include "pv_batch.cuh"
+#include "pv_quadtree.cuh"
 
 using pv::Factors;
 using pv::Geometry;
@@ -39,6 +40,9 @@ struct Layout {
     size_t off_in[6];    // I_s, I_t, g_x, g_y, m_x, m_y
     size_t off_stage_frame, off_stage_normals, off_partials, off_scalars;
     size_t off_desc;     // the sweep kernel's descriptor of this sequence
+    pv::QtGeom q;        // quadtree topology: node levels (n_levels = 0 for the grid)
+    size_t node_bytes;   // one node-state buffer
+    size_t off_node[2];
     size_t total;
 };
 
@@ -58,7 +62,8 @@ bool params_ok(const pixvod_params* p) {
     if (!(std::isfinite(p->damping) && p->damping >= 0 && p->damping < 1)) return false;
     if (p->kf_interval < 0) return false;
     if (p->precision != 32 && p->precision != 64) return false;
-    for (int k = 0; k < 7; ++k)
+    if (p->topology != PIXVOD_TOPOLOGY_GRID && p->topology != PIXVOD_TOPOLOGY_QUADTREE) return false;
+    for (int k = 0; k < 6; ++k)
         if (p->reserved[k] != 0) return false;
     return true;
 }
@@ -92,6 +97,30 @@ Layout make_layout(const pixvod_intrinsics* K, const pixvod_params* p) {
     off += align_up(sizeof(Scalars), kAlign);
     L.off_desc = off;
     off += kDescBytes;
+    L.q.n_levels = 0;
+    L.q.n_nodes = 0;
+    L.q.stride = 0;
+    L.node_bytes = 0;
+    L.off_node[0] = L.off_node[1] = off;
+    if (p->topology == PIXVOD_TOPOLOGY_QUADTREE) {
+        int h = K->height, w = K->width, nodes = 0;
+        while ((h > 1 || w > 1) && L.q.n_levels < pv::QT_MAX_LEVELS) {
+            h = (h + 1) / 2;
+            w = (w + 1) / 2;
+            L.q.h[L.q.n_levels] = h;
+            L.q.w[L.q.n_levels] = w;
+            L.q.base[L.q.n_levels] = nodes;
+            nodes += h * w;
+            L.q.n_levels++;
+        }
+        L.q.n_nodes = nodes;
+        L.q.stride = align_up((size_t)nodes, 64);
+        L.node_bytes = align_up(L.q.stride * pv::NODE_PLANES * L.elt, kAlign);
+        for (int b = 0; b < 2; ++b) {
+            L.off_node[b] = off;
+            off += L.node_bytes;
+        }
+    }
     L.total = off;
     return L;
 }
@@ -283,6 +312,45 @@ void harvest_profile(pixvod_handle* h) {
     h->ev_used = 0;
 }
 
+bool is_quadtree(const pixvod_handle* h) { return h->L.q.n_levels > 0; }
+
+template <typename T>
+T* node_ptr(pixvod_handle* h, int b) {
+    return reinterpret_cast<T*>(h->ws + h->L.off_node[b]);
+}
+
+// arguments of the quadtree sweep reading buffers `cur`, writing `cur ^ 1`
+template <typename T>
+pv::QtArgs<T> qt_args(pixvod_handle* h) {
+    pv::QtArgs<T> a;
+    a.g = geometry<T>(h);
+    a.f = factors<T>(h);
+    a.q = h->L.q;
+    a.in = state_ptr<T>(h, h->cur);
+    a.out = state_ptr<T>(h, h->cur ^ 1);
+    a.nin = node_ptr<T>(h, h->cur);
+    a.nout = node_ptr<T>(h, h->cur ^ 1);
+    a.I_s = input_ptr<T>(h, 0);
+    a.I_t = input_ptr<T>(h, 1);
+    a.g_x = input_ptr<T>(h, 2);
+    a.g_y = input_ptr<T>(h, 3);
+    a.m_x = input_ptr<T>(h, 4);
+    a.m_y = input_ptr<T>(h, 5);
+    a.sc = scalars(h);
+    return a;
+}
+
+// one synchronous sweep of a quadtree handle: pixels and all node levels
+template <typename T>
+pixvod_status launch_qt_sweep(pixvod_handle* h) {
+    const pv::QtArgs<T> a = qt_args<T>(h);
+    pv::k_qt_pixels<T><<<pixel_grid(h), pixel_block(), 0, h->stream>>>(a);
+    pixvod_status s = launched(h);
+    if (s != PIXVOD_OK) return s;
+    pv::k_qt_nodes<T><<<(h->L.q.n_nodes + 127) / 128, 128, 0, h->stream>>>(a);
+    return launched(h);
+}
+
 template <typename T>
 pixvod_status run_sweeps(pixvod_handle* h, int n) {
     pixvod_status st = cuda_status(sweep_attributes<T>());
@@ -294,9 +362,14 @@ pixvod_status run_sweeps(pixvod_handle* h, int n) {
             if (h->ev_used == kProfilePairs) harvest_profile(h);
             cudaEventRecord(h->ev[2 * h->ev_used], h->stream);
         }
-        pv::k_sweeps<T><<<n_tiles, sweep_block(), pv::sweep_smem_bytes<T>(), h->stream>>>(
-            desc_ptr<T>(h), nullptr, n_tiles, 1, h->cur, pv::GridSync{nullptr, nullptr, nullptr});
-        pixvod_status s = launched(h);
+        pixvod_status s;
+        if (is_quadtree(h)) {
+            s = launch_qt_sweep<T>(h);
+        } else {
+            pv::k_sweeps<T><<<n_tiles, sweep_block(), pv::sweep_smem_bytes<T>(), h->stream>>>(
+                desc_ptr<T>(h), nullptr, n_tiles, 1, h->cur, pv::GridSync{nullptr, nullptr, nullptr});
+            s = launched(h);
+        }
         if (prof) {
             cudaEventRecord(h->ev[2 * h->ev_used + 1], h->stream);
             h->ev_used++;
@@ -338,6 +411,10 @@ pixvod_status set_keyframe(pixvod_handle* h, const float* d_frame, const float* 
     if (s != PIXVOD_OK) return s;
     pv::k_reset<T><<<pixel_grid(h), pixel_block(), 0, h->stream>>>(geometry<T>(h), factors<T>(h),
                                                                     state_ptr<T>(h, h->cur), scalars(h));
+    s = launched(h);
+    if (s != PIXVOD_OK || !is_quadtree(h)) return s;
+    pv::k_qt_reset<T><<<(h->L.q.n_nodes + 127) / 128, 128, 0, h->stream>>>(h->L.q, factors<T>(h).lam_P,
+                                                                            node_ptr<T>(h, h->cur));
     return launched(h);
 }
 
@@ -756,6 +833,7 @@ pixvod_status pixvod_save_state(pixvod_handle* h, void* h_buf, size_t bytes) {
 
 pixvod_status pixvod_load_state(pixvod_handle* h, const void* h_buf, size_t bytes) {
     if (!h || !h_buf || bytes != state_blob_bytes(h)) return PIXVOD_EINVAL;
+    if (is_quadtree(h)) return PIXVOD_ESTATE;  // checkpoints hold no node states
     const char* buf = static_cast<const char*>(h_buf);
     const int64_t* hd = reinterpret_cast<const int64_t*>(buf);
     size_t pb = h->L.plane_elems * h->L.elt;
@@ -841,6 +919,7 @@ pixvod_status pixvod_backward_workspace_bytes(const pixvod_intrinsics* K, const 
 pixvod_status pixvod_set_recording(pixvod_handle* h, void* d_workspace, size_t ws_bytes, int32_t max_iters,
                                    int32_t checkpoint_every) {
     if (!h) return PIXVOD_EINVAL;
+    if (is_quadtree(h)) return PIXVOD_ESTATE;  // the adjoint covers the grid topology
     h->rec_valid = false;
     h->rec_n = 0;
     if (!d_workspace) {
@@ -1090,6 +1169,7 @@ extern "C" {
 pixvod_status pixvod_batch_workspace_bytes(int32_t n, const pixvod_intrinsics* K, const pixvod_params* p,
                                            size_t* out_bytes) {
     if (n < 1 || !K || !params_ok(p) || !out_bytes) return PIXVOD_EINVAL;
+    if (p->topology != PIXVOD_TOPOLOGY_GRID) return PIXVOD_EINVAL;  // batches run grid sequences
     for (int i = 0; i < n; ++i)
         if (!intrinsics_ok(&K[i])) return PIXVOD_EINVAL;
     *out_bytes = make_batch_layout(n, K, p).total;
