@@ -359,6 +359,69 @@ def run_gpu(args):
     return 0
 
 
+def run_quadtree(args):
+    """Quadtree workload: the realistic 640x480 sequence tracked with the
+    hierarchical identity topology (pixels plus ten node levels), 20 sweeps per
+    frame; the same frames are also timed with the grid topology."""
+    n_frames = 1 + args.warmup + args.steps
+    frames, normals = render_frames(2, n_frames, 10, max(1, min(16, os.cpu_count() or 2)))
+    import torch
+    import paper_2606_03989_gb300 as pv
+    import synth
+    seq = synth.realistic(2, 1)
+    dev = torch.device("cuda", 0)
+    d_frames = [torch.from_numpy(f).to(dev) for f in frames]
+    d_normals = {k: torch.from_numpy(n).to(dev) for k, n in normals.items()}
+    stream = torch.cuda.Stream(dev)
+    out = {}
+    for topo in (pv.TOPOLOGY_QUADTREE, pv.TOPOLOGY_GRID):
+        params = pv.params(precision=32, kf_interval=10, sigma_P=seq.sigma_P, topology=topo)
+        with torch.cuda.stream(stream):
+            trk = pv.Tracker(seq.cam.as_tuple(), params, dev, stream=stream)
+            for k in range(0, 1 + args.warmup):
+                trk.track(d_frames[k], d_normals.get(k), n_iters=args.sweeps)
+            stream.synchronize()
+            trk.set_profiling(True)
+            n0 = trk.launch_count()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for k in range(1 + args.warmup, n_frames):
+                trk.track(d_frames[k], d_normals.get(k), n_iters=args.sweeps)
+            ev1.record(stream)
+            ev1.synchronize()
+            prof = trk.profile()
+            out[topo] = {"ms": ev0.elapsed_time(ev1), "sweep_ms": prof["sweep_ms"] / max(prof["sweep_launches"], 1),
+                         "launches": trk.launch_count() - n0, "flags": trk.status()}
+            del trk
+    px = W_IMG * H_IMG
+    n_nodes, h, w = 0, H_IMG, W_IMG
+    while h > 1 or w > 1:
+        h, w = (h + 1) // 2, (w + 1) // 2
+        n_nodes += h * w
+    node_bytes = 4 * 2 * 162 * n_nodes            # node planes read and written per sweep
+    q = out[pv.TOPOLOGY_QUADTREE]
+    peak, peak_kind = hbm_peak()
+    bytes_sweep = px * BYTES_PER_PX_SWEEP + node_bytes
+    achieved = bytes_sweep / (q["sweep_ms"] * 1e-3) / 1e9
+    line = {
+        "metric": "Mpixel*GBP-sweeps/s at 640x480, quadtree identity topology", "unit": "Mpx*sweeps/s",
+        "value": px * args.sweeps * args.steps / (q["ms"] * 1e-3) / 1e6, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": q["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "realistic synthetic sequence 640x480 (fx=fy=525), %d GBP sweeps per frame, "
+                               "keyframe every 10 frames, quadtree identity factors (%d node levels, %d nodes)"
+                               % (args.sweeps, 10, n_nodes), "sweeps_per_frame": args.sweeps},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_qt_pixels<float> + k_qt_nodes<float>", "peak_source": peak_kind,
+                     "bytes_per_launch": bytes_sweep, "sweep_ms": q["sweep_ms"]},
+        "grid_same_frames": {"value": px * args.sweeps * args.steps / (out[pv.TOPOLOGY_GRID]["ms"] * 1e-3) / 1e6,
+                             "sweep_ms": out[pv.TOPOLOGY_GRID]["sweep_ms"]},
+        "gpu_launches": q["launches"], "device_flags": q["flags"] | out[pv.TOPOLOGY_GRID]["flags"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(args):
     """Batched workload: 64 sequences of the realistic family at resolutions drawn
     from {128x96, 256x256, 320x240, 640x480}; one step advances every sequence by
@@ -577,8 +640,9 @@ def run_ablation(args):
     normals = [torch.from_numpy(r[3]).to(dev) for r in rendered]
     gt = [seq.relative_pose(0, k) for k in range(n_frames)]
     params = pv.params(precision=32, kf_interval=kf, sigma_P=seq.sigma_P)
+    params_qt = pv.params(precision=32, kf_interval=kf, sigma_P=seq.sigma_P, topology=pv.TOPOLOGY_QUADTREE)
 
-    def track_all(imgs, sweeps):
+    def track_all(imgs, sweeps, params=params):
         trk = pv.Tracker(seq.cam.as_tuple(), params, dev)
         rot, tr = [], []
         for k in range(n_frames):
@@ -591,10 +655,13 @@ def run_ablation(args):
                 "trans_cm_mean": 100 * float(np.mean(tr)), "trans_cm_last": 100 * tr[-1], "flags": trk.status()}
 
     curves = {name: {str(sw): track_all(frames[name], sw) for sw in (5, 10, 20, 40)} for name in frames}
-    basin = {"reset_depth": [], "gt_depth": []}
-    for init in basin:
+    curves["default_quadtree"] = {str(sw): track_all(frames["default"], sw, params_qt) for sw in (5, 10, 20, 40)}
+    basin = {"reset_depth": [], "gt_depth": [], "quadtree_reset_depth": []}   # (load_state: grid only)
+    for key in basin:
+        init = "gt_depth" if key.endswith("gt_depth") else "reset_depth"
+        prm = params_qt if key.startswith("quadtree") else params
         for k in range(1, 13):
-            trk = pv.Tracker(seq.cam.as_tuple(), params, dev)
+            trk = pv.Tracker(seq.cam.as_tuple(), prm, dev)
             trk.track(torch.from_numpy(frames["default"][0]).to(dev), normals[0])
             if init == "gt_depth":
                 _set_keyframe_depth(trk, seq.depth(0))
@@ -603,7 +670,7 @@ def run_ablation(args):
             T = trk.pose_global()
             r1, t1 = _pose_errors(T, gt[k])
             dirn, scale = _translation_shape(T, gt[k])
-            basin[init].append({"frames_apart": k, "init_rot_deg": r0, "init_trans_cm": 100 * t0,
+            basin[key].append({"frames_apart": k, "init_rot_deg": r0, "init_trans_cm": 100 * t0,
                                 "final_rot_deg": r1, "final_trans_cm": 100 * t1,
                                 "trans_dir_err_deg": dirn, "trans_scale": scale, "flags": trk.status()})
     line = {
@@ -644,7 +711,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--sweeps", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="realistic", choices=["realistic", "batched", "adjoint", "ablation"])
+    ap.add_argument("--workload", default="realistic",
+                    choices=["realistic", "batched", "adjoint", "ablation", "quadtree"])
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -658,6 +726,8 @@ def main(argv=None):
         return run_adjoint(args)
     if args.workload == "ablation":
         return run_ablation(args)
+    if args.workload == "quadtree":
+        return run_quadtree(args)
     return run_gpu(args)
 
 
