@@ -344,8 +344,10 @@ __device__ __forceinline__ int qt_level(const QtGeom& q, int n) {
 // children (pixels carry the rank-one photometric part u of their marginal) and
 // from its parent, belief solve, Exp/Log update, projected stores. The damped
 // messages are written to `nout` first and projected there once tau is known.
+// Latency bound (five dependent load-and-solve steps per node): 6 blocks per SM
+// (85 registers, spills served by L1) measured fastest among 3-10 blocks per SM.
 template <typename T>
-__global__ void __launch_bounds__(128) k_qt_nodes(const QtArgs<T> a) {
+__global__ void __launch_bounds__(128, 6) k_qt_nodes(const QtArgs<T> a) {
     const QtGeom& q = a.q;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= q.n_nodes) return;
