@@ -129,8 +129,8 @@ Layout make_layout(const pixvod_intrinsics* K, const pixvod_params* p) {
 // every `every` sweeps, the states of one segment recomputed from a checkpoint,
 // two adjoint states (FP64), descriptors of the recompute launches, the
 // reverse-mode tapes of the adjoint kernel and a few accumulators.
-constexpr int kTapeCap = 9216;            // tape nodes per thread (about 7200 used)
-constexpr int kAdjSlotsPerSM = 128;       // adjoint threads per SM (four blocks)
+constexpr int kTapeCap = 8192;            // tape nodes per thread (at most 7133 seen)
+constexpr int kAdjSlotsPerSM = 256;       // adjoint threads per SM (eight blocks of one warp)
 struct RecLayout {
     int n_ckpt, every, max_iters, slots;
     size_t state_bytes, adj_bytes;
