@@ -261,6 +261,14 @@ pixvod_status pixvod_set_recording(pixvod_handle* h, void* d_workspace, size_t w
 pixvod_status pixvod_backward(pixvod_handle* h, const double* d_grad_xi, const double* d_grad_invdepth,
                               double* d_grad_sigmas, double* d_grad_Is, double* d_grad_It, double* check);
 
+/* Differentiate only the last `last_sweeps` sweeps of a recorded frame in
+ * pixvod_backward (0, the default, = all of them): the state before them is
+ * treated as a constant, a truncation of the unrolled derivative. On inputs where
+ * the sweep map expands, the full unrolled derivative grows roughly geometrically
+ * with the number of sweeps and a short window keeps it bounded. EINVAL if
+ * last_sweeps < 0. */
+pixvod_status pixvod_set_backward_window(pixvod_handle* h, int32_t last_sweeps);
+
 /* ---------------------------------------------------------------------------
  * Batches: many independent sequences (each with its own intrinsics, image size
  * and state, all with the same params) advanced together, one frame per call.

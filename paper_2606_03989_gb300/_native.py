@@ -85,6 +85,7 @@ def _load():
                                                 I32, I32, ctypes.POINTER(ctypes.c_size_t)]),
         "pixvod_set_recording": (S, [H, P, ctypes.c_size_t, I32, I32]),
         "pixvod_backward": (S, [H, P, P, P, P, P, P]),
+        "pixvod_set_backward_window": (S, [H, I32]),
         "pixvod_pose_mean_static": (S, [P, I32, I32, I64, I64, P, P]),
         "pixvod_batch_workspace_bytes": (S, [I32, P, ctypes.POINTER(pixvod_params), ctypes.POINTER(ctypes.c_size_t)]),
         "pixvod_batch_create": (S, [I32, P, ctypes.POINTER(pixvod_params), P, ctypes.c_size_t, P,

@@ -187,6 +187,7 @@ struct pixvod_handle {
     char* rec_ws;
     RecLayout RL;
     int rec_n;           // sweeps of the recorded frame (0: none)
+    int rec_window;      // differentiate only the last rec_window sweeps (0: all)
     bool rec_valid;      // the recorded frame can be differentiated
     // profiling
     bool profiling;
@@ -532,14 +533,17 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
     if (s != PIXVOD_OK) return s;
     A.d_prior = d_prior;
     int a = 0;  // adjoint buffer holding the adjoint of the later state
+    // sweeps first+1 .. n are differentiated; the state after sweep `first` is a constant
+    const int first = h->rec_window > 0 && h->rec_window < n ? n - h->rec_window : 0;
     for (int seg = n_seg - 1; seg >= 0; --seg) {
         const int c = seg * k, len = n - c < k ? n - c : k;
+        if (c + len <= first) break;
         for (int j = 1; j <= len; ++j) {
             pv::k_sweeps<T><<<n_tiles, sweep_block(), pv::sweep_smem_bytes<T>(), st>>>(
                 ddesc + (c + j - 1), nullptr, n_tiles, 1, 0, pv::GridSync{nullptr, nullptr, nullptr});
             if ((s = launched(h)) != PIXVOD_OK) return s;
         }
-        for (int j = len; j >= 1; --j) {
+        for (int j = len; j >= 1 && c + j > first; --j) {
             A.state_in = j == 1 ? ckpt(seg) : segbuf(j - 1);
             A.state_out = segbuf(j);
             A.adj_out = adj[a];
@@ -674,6 +678,7 @@ pixvod_status pixvod_create(const pixvod_intrinsics* K, const pixvod_params* p, 
     h->prof_launch_base = 0;
     h->rec_ws = nullptr;
     h->rec_n = 0;
+    h->rec_window = 0;
     h->rec_valid = false;
     pixvod_status s = cuda_status(cudaMemsetAsync(h->ws, 0, L.total, h->stream));
     if (s == PIXVOD_OK) {
@@ -934,6 +939,12 @@ pixvod_status pixvod_set_recording(pixvod_handle* h, void* d_workspace, size_t w
     if (ws_bytes < R.total) return PIXVOD_ENOMEM;
     h->RL = R;
     h->rec_ws = static_cast<char*>(d_workspace);
+    return PIXVOD_OK;
+}
+
+pixvod_status pixvod_set_backward_window(pixvod_handle* h, int32_t last_sweeps) {
+    if (!h || last_sweeps < 0) return PIXVOD_EINVAL;
+    h->rec_window = last_sweeps;
     return PIXVOD_OK;
 }
 
@@ -1221,6 +1232,7 @@ pixvod_status pixvod_batch_create(int32_t n, const pixvod_intrinsics* K, const p
         h.prof_launch_base = 0;
         h.rec_ws = nullptr;
         h.rec_n = 0;
+        h.rec_window = 0;
         h.rec_valid = false;
     }
     int dev = 0;

@@ -173,6 +173,10 @@ class Tracker:
         nat.check(nat.lib.pixvod_set_recording(self._h, ptr, need.value, int(max_iters), int(checkpoint_every)),
                   "pixvod_set_recording")
 
+    def set_backward_window(self, last_sweeps: int):
+        """Differentiate only the last `last_sweeps` sweeps (0 = all)."""
+        nat.check(nat.lib.pixvod_set_backward_window(self._h, int(last_sweeps)), "pixvod_set_backward_window")
+
     def stop_recording(self):
         nat.check(nat.lib.pixvod_set_recording(self._h, None, 0, 1, 1), "pixvod_set_recording")
         self._rec = None

@@ -62,10 +62,12 @@ def oracle_loss(c, I_s=None, I_t=None, **sig):
     return loss(c, xi, np.exp(-trk.state.mu[..., 6]))
 
 
-def gpu_run(c, precision=64):
+def gpu_run(c, precision=64, window=None):
     seq = c["seq"]
     trk = pv.Tracker(seq.cam.as_tuple(), pv.params(precision=precision, kf_interval=0, sigma_P=seq.sigma_P), DEV)
     trk.set_recording(SWEEPS, EVERY)
+    if window is not None:
+        trk.set_backward_window(window)
     trk.track(torch.from_numpy(c["I_s"]).to(DEV), torch.from_numpy(c["n"]).to(DEV))
     trk.track(torch.from_numpy(c["I_t"]).to(DEV), n_iters=SWEEPS)
     xi = trk.pose()
@@ -174,6 +176,50 @@ def test_fp32_state_gives_close_gradients(case, gpu64):
     for k in ("sigma_D", "sigma_N"):
         assert np.isfinite(float(g32[k]))
         assert float(g32[k]) == pytest.approx(float(g64[k]), rel=0.1)
+
+
+def oracle_loss_window(c, w, I_s=None, I_t=None, **sig):
+    """The loss with the perturbed inputs used in the last w sweeps only (the first
+    SWEEPS - w sweeps run with the base inputs): what a backward window of w
+    sweeps differentiates."""
+    seq = c["seq"]
+    K = oracle_intrinsics(seq.cam)
+    base, pert = oracle_params(seq), oracle_params(seq, **sig)
+    f64 = lambda x: np.asarray(x, np.float64)
+    win0 = gbp.make_window(K, f64(c["I_s"]), c["n"], f64(c["I_t"]), 0.0)
+    win1 = gbp.make_window(K, f64(c["I_s"] if I_s is None else I_s), c["n"], f64(c["I_t"] if I_t is None else I_t), 0.0)
+    st = gbp.reset_state(win0.shape, 0.0, base)
+    for _ in range(SWEEPS - w):
+        st = gbp.sweep(win0, st, base)
+    for _ in range(w):
+        st = gbp.sweep(win1, st, pert)
+    return loss(c, gbp.pose_estimate(st.mu), np.exp(-st.mu[..., 6]))
+
+
+@pytest.mark.parametrize("w", [1, 2])
+def test_backward_window_matches_finite_differences_of_the_last_sweeps(case, w):
+    _, _, _, g = gpu_run(case, 64, window=w)
+    p = pv.params_default()
+    sD, sN = f32(p.sigma_D), f32(p.sigma_N)
+    assert_close(float(g["sigma_D"]), plateau(lambda s: oracle_loss_window(case, w, sigma_D=s), sD, sD), 0.0)
+    assert_close(float(g["sigma_N"]), plateau(lambda s: oracle_loss_window(case, w, sigma_N=s), sN, sN), 0.0)
+    v, u = 5, 7
+    for name in ("I_s", "I_t"):
+        def f(x):
+            img = case[name].astype(np.float64).copy()
+            img[v, u] = x
+            return oracle_loss_window(case, w, **{name: img})
+        fd = plateau(f, float(case[name][v, u]), 1.0)
+        assert_close(float(g[name][v, u]), fd, 1e-2 * abs(fd) + 1e-12)
+
+
+def test_window_covering_every_sweep_is_the_full_derivative(case, gpu64):
+    _, _, _, g = gpu64
+    for w in (0, SWEEPS, SWEEPS + 3):
+        _, _, _, gw = gpu_run(case, 64, window=w)
+        for k in ("sigma_D", "sigma_N"):
+            assert float(gw[k]) == pytest.approx(float(g[k]), rel=1e-10)
+        assert torch.allclose(gw["I_t"], g["I_t"], rtol=1e-10, atol=1e-12 * float(g["I_t"].abs().max()))
 
 
 def test_backward_needs_a_recorded_frame(case):
