@@ -97,9 +97,9 @@ typedef struct {
  *   halved per level). An image of w x h has ceil(w / 2^l) x ceil(h / 2^l) nodes at
  *   level l. The normal-integration factors stay on the pixel grid. A quadtree
  *   handle stores its pixel state in the same layout (identity slot 0 holds the
- *   message from the parent, slots 1..3 are zero); the node states are not in
- *   checkpoints, so pixvod_load_state and the adjoint (pixvod_set_recording) return
- *   ESTATE, and batches take grid handles only. */
+ *   message from the parent, slots 1..3 are zero); its checkpoints append the
+ *   node states (pixvod_save_state). The adjoint (pixvod_set_recording) returns
+ *   ESTATE for a quadtree handle, and batches take grid handles only. */
 #define PIXVOD_TOPOLOGY_GRID 0
 #define PIXVOD_TOPOLOGY_QUADTREE 1
 
@@ -189,6 +189,9 @@ pixvod_status pixvod_get_status(pixvod_handle* h, uint32_t* flags);
  *   [4] height  [5] pitch (elements per plane row)  [6] state planes (151)
  *   [7] frame index  [8] byte offset of the planes  [9] byte offset of the scalars
  *   [10] input planes (6)  [11] 1 if a target frame is loaded
+ *   [12] quadtree nodes n (0 for the grid topology)  [13] node planes (162 for
+ *   the quadtree topology, else 0)  [14] byte offset of the node planes (0 for
+ *   the grid topology); words 15..31 are zero
  * Each plane is height*pitch elements of the state precision. State planes:
  *   0..6     mu: xi_0..xi_5 (theta, rho), log-depth
  *   7..27    M_p: pose information of the belief without the photometric factor
@@ -205,6 +208,14 @@ pixvod_status pixvod_get_status(pixvod_handle* h, uint32_t* flags);
  * m_y (to the lower neighbour).
  * Scalars (doubles): xi_est[6], T_kf[16] (T_kf<-world), T_cur[16], d_prior,
  * d_mean.
+ * Quadtree handles then hold 162 node planes of n elements each (state
+ * precision), nodes numbered level by level from level 1, row-major within a
+ * level. Node planes:
+ *   0..5     pose of the node (theta, rho)
+ *   6..26    belief information: level prior plus the damped messages, packed
+ *   27+27k.. identity-factor message into the node from slot k (k = 0..3 the
+ *            children, 2 (row % 2) + col % 2; k = 4 the parent): 21 packed
+ *            Lambda then 6 eta
  * pixvod_state_size returns the byte count. save and load synchronise the
  * stream (the library's internal state layout differs from this format and is
  * converted on the host); load restores the frame index. EINVAL on a size,

@@ -9,6 +9,7 @@ from __future__ import annotations
 import ctypes
 import os
 from dataclasses import dataclass
+from typing import Optional
 
 import numpy as np
 
@@ -156,6 +157,12 @@ class StateView:
     planes: np.ndarray      # (151, H, W)
     inputs: np.ndarray      # (6, H, W): I_s, I_t, g_x, g_y, m_x, m_y
     scalars: np.ndarray     # (40,)
+    nodes: Optional[np.ndarray] = None   # quadtree handles: (162, n_nodes), else None
+
+    @property
+    def node_pose(self):
+        """(n_nodes, 6) poses of the quadtree nodes, level 1 first (None for the grid)."""
+        return None if self.nodes is None else self.nodes[0:6].T
 
     @property
     def mu(self):
@@ -220,4 +227,9 @@ def parse_state(blob: bytes) -> StateView:
     allp = np.frombuffer(blob, dtype=dt, count=(nplanes + ninp) * H * pitch, offset=off_p)
     allp = allp.reshape(nplanes + ninp, H, pitch)[:, :, :W].astype(np.float64)
     sc = np.frombuffer(blob, dtype=np.float64, count=40, offset=off_s).copy()
-    return StateView(prec, W, H, fidx, bool(has_t), allp[:nplanes], allp[nplanes:], sc)
+    n_nodes, node_planes, off_n = (int(x) for x in np.frombuffer(blob, dtype="<i8", count=15)[12:15])
+    nodes = None
+    if node_planes:
+        nodes = np.frombuffer(blob, dtype=dt, count=node_planes * n_nodes, offset=off_n)
+        nodes = nodes.reshape(node_planes, n_nodes).astype(np.float64)
+    return StateView(prec, W, H, fidx, bool(has_t), allp[:nplanes], allp[nplanes:], sc, nodes)

@@ -581,9 +581,17 @@ constexpr int kScalarDoubles = 40;
 
 constexpr int kBlobPlanes = pv::N_PLANES + pv::N_INPUT_PLANES;
 
-size_t state_blob_bytes(const pixvod_handle* h) {
+// Quadtree handles append the node states after the scalars: NODE_PLANES planes of
+// n_nodes elements each (node index dense over the levels, level 1 first).
+size_t node_blob_offset(const pixvod_handle* h) {
     return kHeaderBytes + h->L.plane_elems * h->L.elt * kBlobPlanes + kScalarDoubles * sizeof(double);
 }
+
+size_t node_blob_bytes(const pixvod_handle* h) {
+    return (size_t)h->L.q.n_nodes * pv::NODE_PLANES * h->L.elt;
+}
+
+size_t state_blob_bytes(const pixvod_handle* h) { return node_blob_offset(h) + node_blob_bytes(h); }
 
 // Checkpoint planes are row-major (height x pitch); the state is tile-major.
 // tile_to_rows / rows_to_tile convert one precision's elements on the host.
@@ -816,6 +824,9 @@ pixvod_status pixvod_save_state(pixvod_handle* h, void* h_buf, size_t bytes) {
     hd[9] = kHeaderBytes + (int64_t)(pb * kBlobPlanes);
     hd[10] = pv::N_INPUT_PLANES;
     hd[11] = h->has_target ? 1 : 0;
+    hd[12] = h->L.q.n_nodes;
+    hd[13] = is_quadtree(h) ? pv::NODE_PLANES : 0;
+    hd[14] = is_quadtree(h) ? (int64_t)node_blob_offset(h) : 0;
     std::vector<char> tiles(h->L.state_bytes);
     pixvod_status s0 = cuda_status(cudaMemcpyAsync(tiles.data(), h->ws + h->L.off_state[h->cur],
                                                    h->L.state_bytes, cudaMemcpyDeviceToHost, h->stream));
@@ -833,19 +844,26 @@ pixvod_status pixvod_save_state(pixvod_handle* h, void* h_buf, size_t bytes) {
     pixvod_status s = cuda_status(cudaMemcpyAsync(buf + hd[9], scalars(h), kScalarDoubles * sizeof(double),
                                                   cudaMemcpyDeviceToHost, h->stream));
     if (s != PIXVOD_OK) return s;
+    if (is_quadtree(h)) {
+        size_t row = (size_t)h->L.q.n_nodes * h->L.elt;
+        s = cuda_status(cudaMemcpy2DAsync(buf + hd[14], row, h->ws + h->L.off_node[h->cur], h->L.q.stride * h->L.elt,
+                                          row, pv::NODE_PLANES, cudaMemcpyDeviceToHost, h->stream));
+        if (s != PIXVOD_OK) return s;
+    }
     return cuda_status(cudaStreamSynchronize(h->stream));
 }
 
 pixvod_status pixvod_load_state(pixvod_handle* h, const void* h_buf, size_t bytes) {
     if (!h || !h_buf || bytes != state_blob_bytes(h)) return PIXVOD_EINVAL;
-    if (is_quadtree(h)) return PIXVOD_ESTATE;  // checkpoints hold no node states
     const char* buf = static_cast<const char*>(h_buf);
     const int64_t* hd = reinterpret_cast<const int64_t*>(buf);
     size_t pb = h->L.plane_elems * h->L.elt;
     if (hd[0] != kMagic || hd[1] != 1 || hd[2] != h->p.precision || hd[3] != h->K.width ||
         hd[4] != h->K.height || hd[5] != h->L.pitch || hd[6] != pv::N_PLANES || hd[7] < 0 ||
         hd[8] != kHeaderBytes || hd[9] != kHeaderBytes + (int64_t)(pb * kBlobPlanes) ||
-        hd[10] != pv::N_INPUT_PLANES || (hd[11] != 0 && hd[11] != 1))
+        hd[10] != pv::N_INPUT_PLANES || (hd[11] != 0 && hd[11] != 1) || hd[12] != h->L.q.n_nodes ||
+        hd[13] != (is_quadtree(h) ? pv::NODE_PLANES : 0) ||
+        hd[14] != (is_quadtree(h) ? (int64_t)node_blob_offset(h) : 0))
         return PIXVOD_EINVAL;
     std::vector<char> tiles(h->L.state_bytes, 0);
     if (h->p.precision == 64)
@@ -863,6 +881,12 @@ pixvod_status pixvod_load_state(pixvod_handle* h, const void* h_buf, size_t byte
     pixvod_status s = cuda_status(cudaMemcpyAsync(scalars(h), buf + hd[9], kScalarDoubles * sizeof(double),
                                                   cudaMemcpyHostToDevice, h->stream));
     if (s != PIXVOD_OK) return s;
+    if (is_quadtree(h)) {
+        size_t row = (size_t)h->L.q.n_nodes * h->L.elt;
+        s = cuda_status(cudaMemcpy2DAsync(h->ws + h->L.off_node[h->cur], h->L.q.stride * h->L.elt, buf + hd[14], row,
+                                          row, pv::NODE_PLANES, cudaMemcpyHostToDevice, h->stream));
+        if (s != PIXVOD_OK) return s;
+    }
     if ((s = cuda_status(cudaStreamSynchronize(h->stream))) != PIXVOD_OK) return s;
     h->frame_index = hd[7];
     h->has_target = hd[11] == 1;

@@ -1,7 +1,8 @@
 """Quadtree identity topology on the GPU (topology = PIXVOD_TOPOLOGY_QUADTREE)
 against the quadtree oracle (oracle/quadtree.py, pinned in
 test_oracle_quadtree.py): the pixel state after 1 and 3 synchronous sweeps from
-the keyframe reset, on 16x12, a ragged 33x17 and 64x48 (six node levels)."""
+the keyframe reset, on 16x12, a ragged 33x17 and 64x48 (six node levels); the
+node states of every level; checkpoints of quadtree handles."""
 import numpy as np
 import pytest
 
@@ -16,7 +17,7 @@ import paper_2606_03989_gb300 as pv  # noqa: E402
 from oracle import gbp  # noqa: E402
 from oracle import quadtree as qt  # noqa: E402
 from helpers import (compressed_from_oracle, compressed_from_view, field_errors, oracle_intrinsics,  # noqa: E402
-                     oracle_params)
+                     oracle_params, pack6)
 
 DEV = torch.device("cuda:0")
 SIZES = [(16, 12), (33, 17), (64, 48)]
@@ -60,6 +61,64 @@ def test_fp64_matches_the_quadtree_oracle(size, sweeps):
     assert np.abs(trk.pose() - gbp.pose_estimate(st.pixels.mu)).max() < 1e-10
 
 
+def oracle_nodes(st) -> dict:
+    """The oracle's node states of all levels (level 1 first, row-major), in the
+    checkpoint's node-plane order: pose, belief information (6x6 pose block,
+    packed) and the messages of slots 0..4 (21 packed Lambda then 6 eta)."""
+    mu = np.concatenate([n.mu[..., :6].reshape(-1, 6) for n in st.nodes])
+    M = np.concatenate([pack6(n.bel_L[..., :6, :6]).reshape(-1, 21) for n in st.nodes])
+    msg = np.concatenate([np.concatenate([pack6(n.msg_L[..., :, :6, :6]), n.msg_eta[..., :, :6]], -1)
+                          .reshape(-1, qt.NODE_SLOTS, 27) for n in st.nodes])
+    return {"mu": mu, "M": M, "msg": msg}
+
+
+@pytest.mark.parametrize("size", SIZES)
+def test_fp64_node_states_match_the_quadtree_oracle(size):
+    """The checkpoint's node planes against the oracle's nodes after 3 sweeps:
+    pose, belief information and the five message slots of every level."""
+    seq = sequence(*size)
+    st, p = oracle_pair(seq, 3)
+    view = run_pair(seq, 64, 3).state()
+    ora = oracle_nodes(st)
+    n = ora["mu"].shape[0]
+    assert view.nodes.shape == (162, n)
+    nd = view.nodes.T
+    got = {"mu": nd[:, 0:6], "M": nd[:, 6:27], "msg": nd[:, 27:162].reshape(n, qt.NODE_SLOTS, 27)}
+    assert np.abs(got["mu"] - ora["mu"]).max() < 1e-8
+    for k in ("M", "msg"):
+        err = np.abs(got[k] - ora[k]).max() / np.abs(ora[k]).max()
+        assert err < 1e-8, (k, err)
+    # the root has no parent
+    assert np.all(got["msg"][-1, qt.NODE_PARENT] == 0.0)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_checkpoint_round_trip_continues_bit_identically(precision):
+    """save after 2 sweeps, load into a fresh quadtree handle, 3 more sweeps on
+    both: the pixel and node states agree bit for bit (the node states are in the
+    checkpoint)."""
+    seq = sequence(33, 17)
+    a = run_pair(seq, precision, 2)
+    blob = a.save_state()
+    p = pv.params(precision=precision, kf_interval=0, sigma_P=seq.sigma_P, topology=pv.TOPOLOGY_QUADTREE)
+    b = pv.Tracker(seq.cam.as_tuple(), p, DEV)
+    b.load_state(blob)
+    assert b.save_state() == blob
+    for t in (a, b):
+        t.sweep(3)
+    va, vb = a.state(), b.state()
+    assert a.status() == 0 and b.status() == 0
+    assert np.array_equal(va.planes, vb.planes) and np.array_equal(va.nodes, vb.nodes)
+    assert np.abs(va.nodes).max() > 0
+
+
+def test_grid_checkpoint_holds_no_nodes():
+    seq = sequence(16, 12)
+    trk = pv.Tracker(seq.cam.as_tuple(), pv.params(kf_interval=0, sigma_P=seq.sigma_P), DEV)
+    trk.track(torch.from_numpy(seq.frame(0)).to(DEV), torch.from_numpy(seq.normals(0)).to(DEV))
+    assert trk.state().nodes is None
+
+
 @pytest.mark.parametrize("size", SIZES)
 def test_fp32_pose_matches_the_quadtree_oracle(size):
     seq = sequence(*size)
@@ -90,8 +149,15 @@ def test_quadtree_refusals():
     trk = run_pair(seq, 32, 1)
     blob = trk.save_state()
     import ctypes
+    # a grid handle of the same image takes no quadtree checkpoint, nor the reverse
+    g = pv.Tracker(seq.cam.as_tuple(), pv.params(kf_interval=0), DEV)
     buf = ctypes.create_string_buffer(blob, len(blob))
-    assert pv.lib.pixvod_load_state(trk._h, buf, len(blob)) == pv.ESTATE
+    assert pv.lib.pixvod_load_state(g._h, buf, len(blob)) == pv.EINVAL
+    gb = g.save_state()
+    assert pv.lib.pixvod_load_state(trk._h, ctypes.create_string_buffer(gb, len(gb)), len(gb)) == pv.EINVAL
+    bad = bytearray(blob)
+    bad[12 * 8] ^= 1    # node count
+    assert pv.lib.pixvod_load_state(trk._h, ctypes.create_string_buffer(bytes(bad), len(bad)), len(bad)) == pv.EINVAL
     z = torch.zeros(1 << 20, dtype=torch.uint8, device=DEV)
     assert pv.lib.pixvod_set_recording(trk._h, (z.data_ptr() + 255) // 256 * 256, 1 << 19, 5, 1) == pv.ESTATE
     K = pv.intrinsics(*seq.cam.as_tuple())
