@@ -121,7 +121,6 @@ __device__ __forceinline__ Rev v_div(const Rev& a, const Rev& b) { return a / b;
 
 // series limits of the reverse-mode scalar: those of double
 template <> struct Prec<ad::Rev> {
-    static constexpr double tiny = Prec<double>::tiny;
     static constexpr int c_terms = Prec<double>::c_terms;
     static constexpr double d_series_max = Prec<double>::d_series_max;
     static constexpr double ab_series_max = Prec<double>::ab_series_max;

@@ -486,7 +486,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty
             J[5] = b[2];
             J[6] = b[0] * Xs[0] + b[1] * Xs[1] + b[2] * Xs[2];
             T M = v_abs(r) * F.inv_sigma_D;
-            T w = M > F.t_huber ? (T(2) * F.t_huber * M - F.t_huber * F.t_huber) / (M * M) : T(1);
+            T w = M > F.t_huber ? v_div(T(2) * F.t_huber * M - F.t_huber * F.t_huber, M * M) : T(1);
             alpha = w * F.lam_D;
             rph = r;
         }

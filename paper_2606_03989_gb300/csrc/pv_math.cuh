@@ -38,40 +38,47 @@ __device__ __forceinline__ double v_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float v_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double v_div(double a, double b) { return a / b; }
 
-// Precision-dependent series limits: below `tiny` the A/B quotients use two
-// Taylor terms; below 1 rad the C and D coefficients use their power series
-// with enough terms for the type's epsilon.
+// Precision-dependent series limits: below ab_series_max the A/B quotients use
+// their power series to t^6; below 1 rad (C) and d_series_max (D) the other
+// coefficients use their power series with enough terms for the type's epsilon.
 template <typename T> struct Prec;
-// Float: below ab_series_max = 0.3 rad, A and B use their power series to t^6
-// (truncation below 2e-10) and the logarithm recovers the angle from
-// s = sin(t) with the arcsine series to s^9 when s < 0.2 and cos(t) > 0
-// (truncation below 5e-10), so small rotations need no trigonometric calls.
+// Float: below ab_series_max = 0.3 rad the A/B series truncate below 2e-10, and
+// the logarithm recovers the angle from s = sin(t) with the arcsine series to
+// s^9 when s < 0.2 and cos(t) > 0 (truncation below 5e-10), so small rotations
+// need no trigonometric calls.
 template <> struct Prec<float> {
-    static constexpr float tiny = 1e-4f;
     static constexpr int c_terms = 7;
     static constexpr float d_series_max = 1.0f;
     static constexpr float ab_series_max = 0.3f;
     static constexpr float asin_series_max = 0.2f;
 };
 template <> struct Prec<double> {
-    static constexpr double tiny = 1e-8;
     static constexpr int c_terms = 12;
     static constexpr double d_series_max = 0.5;
     static constexpr double ab_series_max = 1e-8;
     static constexpr double asin_series_max = 0.0;
 };
 
-// (t - sin t)/t^3 = sum_k (-1)^k t^(2k) / (2k+3)!
+// (t - sin t)/t^3 = sum_k (-1)^k t^(2k) / (2k+3)!, k < c_terms, evaluated in
+// Horner form with the coefficients computed at compile time
+__host__ __device__ constexpr double series_C_coef(int k) {
+    double f = 1.0;
+    for (int i = 2; i <= 2 * k + 3; ++i) f *= double(i);
+    return (k % 2 ? -1.0 : 1.0) / f;
+}
+
+template <typename T, int K, int N>
+__device__ __forceinline__ T series_C_from(T t2) {
+    constexpr double c = series_C_coef(K);
+    if constexpr (K + 1 < N)
+        return T(c) + t2 * series_C_from<T, K + 1, N>(t2);
+    else
+        return T(c);
+}
+
 template <typename T>
 __device__ __forceinline__ T series_C(T t2) {
-    T term = T(1) / T(6);
-    T sum = term;
-#pragma unroll
-    for (int k = 1; k < Prec<T>::c_terms; ++k) {
-        term = -term * t2 / T((2 * k + 2) * (2 * k + 3));
-        sum += term;
-    }
-    return sum;
+    return series_C_from<T, 0, Prec<T>::c_terms>(t2);
 }
 
 // D(t) = (1 - A/(2B))/t^2 = 1/t^2 - cot(t/2)/(2t), the [theta]x^2 coefficient of
@@ -83,17 +90,17 @@ __device__ __forceinline__ T series_D(T t2) {
            t2 * (T(1) / T(47900160) + t2 * (T(1) / T(1892437580.3183))))));
 }
 
+// sin t / t = 1 - t^2/3! + t^4/5! - t^6/7!; (1 - cos t)/t^2 = 1/2! - t^2/4! + t^4/6! - t^6/8!
+template <typename T>
+__device__ __forceinline__ void series_AB(T t2, T* A, T* B) {
+    *A = T(1) - t2 * (T(1) / T(6) - t2 * (T(1) / T(120) - t2 * (T(1) / T(5040))));
+    *B = T(0.5) - t2 * (T(1) / T(24) - t2 * (T(1) / T(720) - t2 * (T(1) / T(40320))));
+}
+
 template <typename T>
 __device__ __forceinline__ void coef_AB(T t, T* A, T* B) {
     if (t < Prec<T>::ab_series_max) {
-        // sin t / t = 1 - t^2/3! + t^4/5! - t^6/7!; (1 - cos t)/t^2 = 1/2! - t^2/4! + t^4/6! - t^6/8!
-        T t2 = t * t;
-        *A = T(1) - t2 * (T(1) / T(6) - t2 * (T(1) / T(120) - t2 * (T(1) / T(5040))));
-        *B = T(0.5) - t2 * (T(1) / T(24) - t2 * (T(1) / T(720) - t2 * (T(1) / T(40320))));
-    } else if (t < Prec<T>::tiny) {
-        T t2 = t * t;
-        *A = T(1) - t2 / T(6);
-        *B = T(0.5) - t2 / T(24);
+        series_AB(t * t, A, B);
     } else {
         T s, c, sh, ch;
         v_sincos(t, &s, &c);
@@ -155,42 +162,54 @@ __device__ __forceinline__ void so3_poly(const T* w, T a, T b, T* M) {
     M[7] = a * w[0] + b * w[1] * w[2];
 }
 
-// Exp: xi (6) -> R (9), t (3)
+// Exp: xi (6) -> R (9), t (3). Below ab_series_max the coefficients come from
+// their power series in t^2, so small rotations take no square root, division
+// or trigonometric call.
 template <typename T>
 __device__ __forceinline__ void se3_exp(const T* xi, T* R, T* t) {
-    T th = v_sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
-    T A, B;
-    coef_AB(th, &A, &B);
-    T C = coef_C(th, A);
+    T t2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    T A, B, C;
+    if (t2 < Prec<T>::ab_series_max * Prec<T>::ab_series_max) {
+        series_AB(t2, &A, &B);
+        C = series_C(t2);
+    } else {
+        T th = v_sqrt(t2);
+        coef_AB(th, &A, &B);
+        C = coef_C(th, A);
+    }
     so3_poly(xi, A, B, R);
     T V[9];
     so3_poly(xi, B, C, V);
     mat3_vec(V, xi + 3, t);
 }
 
-// Log: R (9), t (3) -> xi (6); rotation angles below pi
+// Log: R (9), t (3) -> xi (6); rotation angles below pi. With w = vee(R - R^T)/2,
+// s = |w| = sin(t) and c = cos(t): theta = w t / s = w / A. For s below
+// asin_series_max (and c > 0) t / s = asin(s) / s comes from the arcsine series
+// 1 + s^2/6 + 3 s^4/40 + 5 s^6/112 + 35 s^8/1152 and t^2 = s^2 (t / s)^2, so small
+// rotations take no square root, division or trigonometric call.
 template <typename T>
 __device__ __forceinline__ void se3_log(const T* R, const T* t, T* xi) {
+    static_assert(Prec<T>::asin_series_max <= Prec<T>::d_series_max / 2, "series D range");
     T w0 = T(0.5) * (R[7] - R[5]);
     T w1 = T(0.5) * (R[2] - R[6]);
     T w2 = T(0.5) * (R[3] - R[1]);
-    T s = v_sqrt(w0 * w0 + w1 * w1 + w2 * w2);
+    T s2 = w0 * w0 + w1 * w1 + w2 * w2;
     T c = T(0.5) * (R[0] + R[4] + R[8] - T(1));
-    T th;
-    if (s < Prec<T>::asin_series_max && c > T(0)) {
-        // asin s = s + s^3/6 + 3 s^5/40 + 5 s^7/112 + 35 s^9/1152
-        T s2 = s * s;
-        th = s * (T(1) + s2 * (T(1) / T(6) + s2 * (T(3) / T(40) + s2 * (T(5) / T(112) + s2 * (T(35) / T(1152))))));
+    T ratio, D;
+    if (s2 < Prec<T>::asin_series_max * Prec<T>::asin_series_max && c > T(0)) {
+        ratio = T(1) + s2 * (T(1) / T(6) + s2 * (T(3) / T(40) + s2 * (T(5) / T(112) + s2 * (T(35) / T(1152)))));
+        D = series_D(s2 * ratio * ratio);
     } else {
-        th = v_atan2(s, c);
+        T th = v_atan2(v_sqrt(s2), c);
+        T A, B;
+        coef_AB(th, &A, &B);
+        ratio = T(1) / A;
+        D = coef_D(th, A, B);
     }
-    T A, B;
-    coef_AB(th, &A, &B);
-    T inv = T(1) / A;
-    xi[0] = w0 * inv;
-    xi[1] = w1 * inv;
-    xi[2] = w2 * inv;
-    T D = coef_D(th, A, B);
+    xi[0] = w0 * ratio;
+    xi[1] = w1 * ratio;
+    xi[2] = w2 * ratio;
     T Vi[9];
     so3_poly(xi, T(-0.5), D, Vi);
     mat3_vec(Vi, t, xi + 3);

@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(128) k_qt_pixels(const QtArgs<T> a) {
             J[5] = b[2];
             J[6] = b[0] * Xs[0] + b[1] * Xs[1] + b[2] * Xs[2];
             const T M = v_abs(r) * F.inv_sigma_D;
-            const T w = M > F.t_huber ? (T(2) * F.t_huber * M - F.t_huber * F.t_huber) / (M * M) : T(1);
+            const T w = M > F.t_huber ? v_div(T(2) * F.t_huber * M - F.t_huber * F.t_huber, M * M) : T(1);
             alpha = w * F.lam_D;
             rph = r;
         }
