@@ -246,8 +246,10 @@ __device__ __forceinline__ T ld_state(const T* p) {
 // Thread block of the sweep kernel: one state tile (32 x 4 pixels), one thread
 // per pixel; 4 blocks per SM (55 KB of shared memory and at most 128 registers
 // each). Each thread keeps its four damped identity messages in shared memory
-// until the belief solve has given tau (they are then projected and written), so
-// the direction loop is not unrolled; the normal messages stay in registers.
+// until the belief solve has given tau; their eta is then projected in place and
+// the tile's 108 message planes leave with one bulk copy. The identity-message
+// loop is not unrolled; the normal messages are computed in a loop of their own
+// after it and stay in registers.
 constexpr int SWEEP_BX = TILE_W;
 constexpr int SWEEP_BY = TILE_H;
 constexpr int SWEEP_THREADS = TILE_PX;
@@ -257,28 +259,19 @@ constexpr size_t sweep_smem_bytes() {
     return sizeof(T) * MSG_PLANES * TILE_PX;
 }
 
-// One synchronous sweep over one state tile (tx, ty) by the calling block. The
-// block must have initialised `bar` (one arrival); `parity` is the phase this
-// tile's bulk copy completes. The caller synchronises the block before reusing
-// `msg` for another tile.
+// The calling thread's pixel of the sweep over tile (tx, ty): everything but the
+// store of the identity messages, which are left, projected, in `msg`. False if
+// the tile's bulk copy never arrived (FLAG_TIMEOUT is set).
 template <typename T>
-__device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty, T* msg, uint64_t* bar,
-                                           unsigned parity) {
+__device__ __forceinline__ bool sweep_pixel(const SweepArgs<T>& a, int tx, int ty, T* msg, uint64_t* bar,
+                                            unsigned parity) {
     const int tid = threadIdx.y * SWEEP_BX + threadIdx.x;
     const int u = tx * SWEEP_BX + threadIdx.x;
     const int v = ty * SWEEP_BY + threadIdx.y;
     const Geometry<T>& g = a.g;
     const Factors<T>& F = a.f;
     const size_t tile = (size_t)ty * g.tiles_x + tx;
-    if (tid == 0) {
-        // order earlier generic-proxy accesses (global stores of a previous sweep in
-        // the same launch, shared-memory use of a previous tile) before the async copy
-        asm volatile("fence.proxy.async;" ::: "memory");
-        constexpr unsigned bytes = sizeof(T) * MSG_PLANES * TILE_PX;
-        mbar_expect_tx(bar, bytes);
-        bulk_copy_g2s(msg, a.in + tile * TILE_WORDS + PL_ID * TILE_PX, bytes, bar);
-    }
-    if (u >= g.W || v >= g.H) return;
+    if (u >= g.W || v >= g.H) return true;
     const int i = v * g.pitch + u;
     const T* __restrict__ Si = a.in + tile * TILE_WORDS + tid;   // this pixel, plane 0
     T* __restrict__ Di = a.out + tile * TILE_WORDS + tid;
@@ -316,10 +309,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty
         // the tile's messages never arrived: flag it, wait once more, leave the tile
         atomicOr(&a.sc->flags, FLAG_TIMEOUT);
         mbar_wait_bounded(bar, parity);
-        return;
+        return false;
     }
     const T beta = F.beta, omb = T(1) - F.beta;
-    T nl0 = T(0), ne0 = T(0), nl1 = T(0), ne1 = T(0), nl2 = T(0), ne2 = T(0), nl3 = T(0), ne3 = T(0);
 #pragma unroll 1
     for (int k = 0; k < 4; ++k) {
         T* mb = msg + (k * ID_STRIDE) * TILE_PX + tid;          // identity slot k
@@ -333,38 +325,41 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty
         }
         const int ko = k ^ 1;
         const T* Sj = a.in + state_index(un, vn, g.tiles_x);
+        // variable-to-factor marginal of j: V = W + u u^T with W = M_p,j - Lambda_{f->j}
+        // (pose prior plus j's three other identity messages) and u = u_j, and
+        // eta_v = -eta_{f->j}. All of j's loads are issued here, ahead of the Exp/Log
+        // chain of the residual, so that their latency overlaps it.
+        const T* mj = Sj + (PL_ID + ID_STRIDE * ko) * TILE_PX;
+        T W[21], C[21], z[6], gv[6];
+        T uz = T(0), ur = T(0), uh = T(0);
+        T uj[6], xj[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) xj[q] = ld_state(Sj + q * TILE_PX);
+#pragma unroll
+        for (int q = 0; q < 21; ++q) W[q] = ld_state(Sj + (PL_MP + q) * TILE_PX) - ld_state(mj + q * TILE_PX);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            uj[q] = ld_state(Sj + (PL_U + q) * TILE_PX);
+            gv[q] = -ld_state(mj + (21 + q) * TILE_PX);
+        }
         // identity factor (Eq. 5): r = Log(Exp(xi_j)^-1 Exp(xi_i)), J_i = I, J_j = -I
         T rb[6];
         {
-            T xj[6];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) xj[q] = ld_state(Sj + q * TILE_PX);
             T Rj[9], tj[3], Rr[9], tr[3];
             se3_exp(xj, Rj, tj);
             se3_invmul(Rj, tj, R, t, Rr, tr);
             se3_log(Rr, tr, rb);
         }
-        // variable-to-factor marginal of j: V = W + u u^T with W = M_p,j - Lambda_{f->j}
-        // (pose prior plus j's three other identity messages) and u = u_j
-        const T* mj = Sj + (PL_ID + ID_STRIDE * ko) * TILE_PX;
-        T W[21], C[21], z[6], gv[6];
-        T uz = T(0), ur = T(0), uh = T(0);
         {
-            T uj[6];
 #pragma unroll
-            for (int q = 0; q < 21; ++q) {
-                W[q] = ld_state(Sj + (PL_MP + q) * TILE_PX) - ld_state(mj + q * TILE_PX);
-                C[q] = W[q];
-            }
-#pragma unroll
-            for (int q = 0; q < 6; ++q) uj[q] = ld_state(Sj + (PL_U + q) * TILE_PX);
-            // g0 = eta_v - W r with eta_v = -eta_{f->j}
+            for (int q = 0; q < 21; ++q) C[q] = W[q];
+            // g0 = eta_v - W r
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
                 T wr = T(0);
 #pragma unroll
                 for (int c = 0; c < 6; ++c) wr += W[pidx(q, c)] * rb[c];
-                gv[q] = -ld_state(mj + (21 + q) * TILE_PX) - wr;
+                gv[q] -= wr;
             }
             // A = W + lam_R I is well conditioned (its eigenvalues are at least lam_R);
             // the rank-one u u^T, which can be far larger, stays out of the factorisation
@@ -415,7 +410,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty
             }
         }
 
-        // normal-integration factor (Eq. 6): r_i = d_i - d_j + sg m
+    }
+
+    // normal-integration factors (Eq. 6): r_i = d_i - d_j + sg m
+    T nl[4], ne[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        nl[k] = T(0);
+        ne[k] = T(0);
+        const int un = u + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+        const int vn = v + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+        if (!(un >= 0 && un < g.W && vn >= 0 && vn < g.H)) continue;
+        const int ko = k ^ 1;
+        const T* Sj = a.in + state_index(un, vn, g.tiles_x);
         T dj = ld_state(Sj + 6 * TILE_PX);
         T sv = ld_state(Sj + PL_S * TILE_PX) - ld_state(Sj + (PL_NM + 2 * ko) * TILE_PX);
         T evn = -ld_state(Sj + (PL_NM + 2 * ko + 1) * TILE_PX);
@@ -423,14 +430,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty
         T sg = (k == 0 || k == 2) ? T(1) : T(-1);
         T rn = d - dj + sg * m;
         T den = v_div(T(1), F.lam_N + sv);
-        T nnew = omb * (F.lam_N * sv * den) + beta * ld_state(Si + (PL_NM + 2 * k) * TILE_PX);
-        T enew = omb * (F.lam_N * (evn - sv * rn) * den) + beta * ld_state(Si + (PL_NM + 2 * k + 1) * TILE_PX);
-        md += nnew;
-        eb[6] += enew;
-        if (k == 0) { nl0 = nnew; ne0 = enew; }
-        else if (k == 1) { nl1 = nnew; ne1 = enew; }
-        else if (k == 2) { nl2 = nnew; ne2 = enew; }
-        else { nl3 = nnew; ne3 = enew; }
+        nl[k] = omb * (F.lam_N * sv * den) + beta * ld_state(Si + (PL_NM + 2 * k) * TILE_PX);
+        ne[k] = omb * (F.lam_N * (evn - sv * rn) * den) + beta * ld_state(Si + (PL_NM + 2 * k + 1) * TILE_PX);
+        md += nl[k];
+        eb[6] += ne[k];
     }
 
     T alpha = T(0), rph = T(0);
@@ -560,33 +563,65 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty
         Di[PL_S * TILE_PX] = md + v_div(alpha * J[6] * J[6], T(1) + alpha * qv);
     }
     // messages, projected: eta <- eta - Lambda tau
-    Di[(PL_NM + 0) * TILE_PX] = nl0;
-    Di[(PL_NM + 1) * TILE_PX] = ne0 - nl0 * tau[6];
-    Di[(PL_NM + 2) * TILE_PX] = nl1;
-    Di[(PL_NM + 3) * TILE_PX] = ne1 - nl1 * tau[6];
-    Di[(PL_NM + 4) * TILE_PX] = nl2;
-    Di[(PL_NM + 5) * TILE_PX] = ne2 - nl2 * tau[6];
-    Di[(PL_NM + 6) * TILE_PX] = nl3;
-    Di[(PL_NM + 7) * TILE_PX] = ne3 - nl3 * tau[6];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        Di[(PL_NM + 2 * k) * TILE_PX] = nl[k];
+        Di[(PL_NM + 2 * k + 1) * TILE_PX] = ne[k] - nl[k] * tau[6];
+    }
 #pragma unroll 1
     for (int k = 0; k < 4; ++k) {
-        const T* mb = msg + (k * ID_STRIDE) * TILE_PX + tid;
-        T* dk = Di + (PL_ID + ID_STRIDE * k) * TILE_PX;
+        T* mb = msg + (k * ID_STRIDE) * TILE_PX + tid;
         T L[21];
 #pragma unroll
-        for (int q = 0; q < 21; ++q) {
-            L[q] = mb[q * TILE_PX];
-            dk[q * TILE_PX] = L[q];
-        }
+        for (int q = 0; q < 21; ++q) L[q] = mb[q * TILE_PX];
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
             T e = mb[(21 + r) * TILE_PX];
 #pragma unroll
             for (int c = 0; c < 6; ++c) e -= L[pidx(r, c)] * tau[c];
-            dk[(21 + r) * TILE_PX] = e;
+            mb[(21 + r) * TILE_PX] = e;
         }
     }
     if (flags) atomicOr(&a.sc->flags, flags);
+    return true;
+}
+
+// shared -> global bulk copy by the calling thread, waited for until the writes
+// are complete and ordered before the thread's later generic-proxy accesses;
+// dst, src and bytes must be multiples of 16 bytes
+__device__ __forceinline__ void bulk_copy_s2g(void* dst, const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// One synchronous sweep over one state tile (tx, ty) by the calling block (every
+// thread of the block must call it). The block must have initialised `bar` (one
+// arrival); `parity` is the phase this tile's bulk copy completes. The caller
+// synchronises the block before reusing `msg` for another tile. The message
+// planes of pixels outside the image are copied through unchanged.
+template <typename T>
+__device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty, T* msg, uint64_t* bar,
+                                           unsigned parity) {
+    const int tid = threadIdx.y * SWEEP_BX + threadIdx.x;
+    const size_t tile = (size_t)ty * a.g.tiles_x + tx;
+    constexpr unsigned bytes = sizeof(T) * MSG_PLANES * TILE_PX;
+    if (tid == 0) {
+        // order earlier generic-proxy accesses (global stores of a previous sweep in
+        // the same launch, shared-memory use of a previous tile) before the async copy
+        asm volatile("fence.proxy.async;" ::: "memory");
+        mbar_expect_tx(bar, bytes);
+        bulk_copy_g2s(msg, a.in + tile * TILE_WORDS + PL_ID * TILE_PX, bytes, bar);
+    }
+    const bool ok = sweep_pixel(a, tx, ty, msg, bar, parity);
+    // the projected messages written to shared memory (generic proxy) are read by
+    // the bulk copy (async proxy): fence, then gather the block; a tile whose
+    // messages never arrived is not stored
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (__syncthreads_and(ok) && tid == 0) bulk_copy_s2g(a.out + tile * TILE_WORDS + PL_ID * TILE_PX, msg, bytes);
 }
 
 // ---------------------------------------------------------------------------
