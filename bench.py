@@ -412,7 +412,7 @@ def run_quadtree(args):
                                "keyframe every 10 frames, quadtree identity factors (%d node levels, %d nodes)"
                                % (args.sweeps, 10, n_nodes), "sweeps_per_frame": args.sweeps},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_qt_pixels<float> + k_qt_nodes<float>", "peak_source": peak_kind,
+                     "traffic": None, "kernel": "k_qt_pixels<float> + k_qt_node_msgs<float> + k_qt_node_belief<float>", "peak_source": peak_kind,
                      "bytes_per_launch": bytes_sweep, "sweep_ms": q["sweep_ms"]},
         "grid_same_frames": {"value": px * args.sweeps * args.steps / (out[pv.TOPOLOGY_GRID]["ms"] * 1e-3) / 1e6,
                              "sweep_ms": out[pv.TOPOLOGY_GRID]["sweep_ms"]},

@@ -348,7 +348,15 @@ pixvod_status launch_qt_sweep(pixvod_handle* h) {
     pv::k_qt_pixels<T><<<pixel_grid(h), pixel_block(), 0, h->stream>>>(a);
     pixvod_status s = launched(h);
     if (s != PIXVOD_OK) return s;
-    pv::k_qt_nodes<T><<<(h->L.q.n_nodes + 127) / 128, 128, 0, h->stream>>>(a);
+    {
+        const pv::QtGeom& q = h->L.q;
+        const size_t n_px = (size_t)h->L.tiles_x * h->L.tiles_y * pv::TILE_PX;
+        const size_t n_up = q.n_levels > 1 ? (size_t)(q.n_nodes - q.base[1]) : 0;
+        const size_t threads = n_px + 4 * ((n_up + 31) / 32 * 32) + (size_t)q.n_nodes;
+        pv::k_qt_node_msgs<T><<<(unsigned)((threads + 127) / 128), 128, 0, h->stream>>>(a);
+    }
+    if ((s = launched(h)) != PIXVOD_OK) return s;
+    pv::k_qt_node_belief<T><<<(h->L.q.n_nodes + 127) / 128, 128, 0, h->stream>>>(a);
     return launched(h);
 }
 

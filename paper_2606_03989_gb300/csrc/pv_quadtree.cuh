@@ -2,8 +2,9 @@
 // graph; Sec. 4.2: sigma_R and sigma_P halved per level). Pixels keep the state
 // layout of the grid sweep, using identity slot 0 for the factor to their level-1
 // node; pose nodes of every level live in one structure-of-arrays buffer. One
-// synchronous sweep = k_qt_pixels + k_qt_nodes, both reading the `in` buffers and
-// writing the `out` buffers.
+// synchronous sweep = k_qt_pixels + k_qt_node_msgs + k_qt_node_belief: the first
+// two read only the `in` buffers, the third the node messages the second wrote,
+// and all write the `out` buffers.
 #pragma once
 
 #include "pv_kernels.cuh"
@@ -340,32 +341,178 @@ __device__ __forceinline__ int qt_level(const QtGeom& q, int n) {
     return lvl;
 }
 
-// One node's sweep update: pose prior (sigma_P / 2^l), identity messages from its
-// children (pixels carry the rank-one photometric part u of their marginal) and
-// from its parent, belief solve, Exp/Log update, projected stores. The damped
-// messages are written to `nout` first and projected there once tau is known.
-// Latency bound (five dependent load-and-solve steps per node): 6 blocks per SM
-// (85 registers, spills served by L1) measured fastest among 3-10 blocks per SM.
+// Node update, in two launches per sweep. A node's five messages (children
+// 0..3, parent 4) are independent given the input state, so they are computed by
+// one thread each (k_qt_node_msgs); one thread per node then forms the belief,
+// updates the pose and projects the messages (k_qt_node_belief). With one thread
+// per node doing all five slots in sequence, the 102k nodes of a 640x480 image
+// fit in a single wave and the sweep waited on that chain of dependent
+// load-and-solve steps.
+
+// row, column, level and level-wise scale 4^(l-1) of node n
+struct NodePos {
+    int lvl, r, c;
+};
+__device__ __forceinline__ NodePos node_pos(const QtGeom& q, int n) {
+    NodePos p;
+    p.lvl = qt_level(q, n);
+    const int idx = n - q.base[p.lvl - 1];
+    p.r = idx / q.w[p.lvl - 1];
+    p.c = idx % q.w[p.lvl - 1];
+    return p;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(128, 6) k_qt_nodes(const QtArgs<T> a) {
+__device__ __forceinline__ T level_scale(int lvl) {
+    T s = T(1);
+    for (int k = 0; k < lvl - 1; ++k) s *= T(4);
+    return s;
+}
+
+// One thread per node message: the damped identity message into node n from its
+// slot k (children 2 (row % 2) + col % 2, parent 4), written unprojected to the
+// node's output slot (zero where the slot has no partner: a child outside the
+// level below, the root's parent). Threads, in order: one per pixel in tile
+// order (the child slot of its level-1 node, so that the pixel loads coalesce),
+// then the child slots of the nodes of levels >= 2 (slot-major), then the parent
+// slot of every node. Each thread issues all its loads before any arithmetic.
+template <typename T>
+__global__ void __launch_bounds__(128, 4) k_qt_node_msgs(const QtArgs<T> a) {
     const QtGeom& q = a.q;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= q.n_nodes) return;
     const Geometry<T>& g = a.g;
     const Factors<T>& F = a.f;
     const size_t st = q.stride;
-    const int lvl = qt_level(q, n);
-    const int idx = n - q.base[lvl - 1];
-    const int r = idx / q.w[lvl - 1], c = idx % q.w[lvl - 1];
+    const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int tiles_y = (g.H + TILE_H - 1) / TILE_H;
+    const size_t n_px = (size_t)g.tiles_x * tiles_y * TILE_PX;
+    const int n_up = q.n_levels > 1 ? q.n_nodes - q.base[1] : 0;     // nodes of levels >= 2
+    const size_t n_up_p = ((size_t)n_up + 31) / 32 * 32;
+    int n, k, lvl, r, c;
+    const T* S = nullptr;      // sender: child pixel (tile-major state) ...
+    const T* C = nullptr;      // ... or node (node planes)
+    const T* ms = nullptr;     // the sender's stored message on the shared factor
+    T lam;
+    if (gid < n_px) {
+        // a level-1 node's child slot, one thread per pixel in tile order
+        const int tile = (int)(gid / TILE_PX), lane = (int)(gid % TILE_PX);
+        const int u = (tile % g.tiles_x) * TILE_W + lane % TILE_W;
+        const int v = (tile / g.tiles_x) * TILE_H + lane / TILE_W;
+        if (u >= g.W || v >= g.H) return;
+        lvl = 1;
+        r = v / 2;
+        c = u / 2;
+        n = qt_node(q, 1, r, c);
+        k = 2 * (v % 2) + u % 2;
+        S = a.in + state_index(u, v, g.tiles_x);
+        lam = F.lam_R;
+        // child slots of this node without a pixel (odd width or height) are zeroed
+        // by the pixel before them
+        const bool nx = u % 2 == 0 && u + 1 >= g.W, ny = v % 2 == 0 && v + 1 >= g.H;
+        if (nx || ny) {
+            T* z0 = a.nout + n + NP_MSG * st;
+            for (int m = 0; m < ID_STRIDE; ++m) {
+                if (nx) z0[(ID_STRIDE * (k + 1) + m) * st] = T(0);
+                if (ny) z0[(ID_STRIDE * (k + 2) + m) * st] = T(0);
+                if (nx && ny) z0[(ID_STRIDE * (k + 3) + m) * st] = T(0);
+            }
+        }
+    } else if (gid < n_px + 4 * n_up_p) {
+        // child slot k of a node of level >= 2
+        const size_t g2 = gid - n_px;
+        k = (int)(g2 / n_up_p);
+        const int j = (int)(g2 % n_up_p);
+        if (j >= n_up) return;
+        n = q.base[1] + j;
+        const NodePos p = node_pos(q, n);
+        lvl = p.lvl;
+        r = p.r;
+        c = p.c;
+        const int rc = 2 * r + k / 2, cc = 2 * c + k % 2;
+        if (rc < q.h[lvl - 2] && cc < q.w[lvl - 2]) {
+            C = a.nin + qt_node(q, lvl - 1, rc, cc);
+            ms = C + (NP_MSG + ID_STRIDE * NP_PARENT) * st;
+        }
+        lam = F.lam_R * level_scale<T>(lvl);                     // sigma_R / 2^(l-1)
+    } else {
+        // parent slot of every node
+        const size_t g3 = gid - n_px - 4 * n_up_p;
+        if (g3 >= (size_t)q.n_nodes) return;
+        n = (int)g3;
+        k = NP_PARENT;
+        const NodePos p = node_pos(q, n);
+        lvl = p.lvl;
+        r = p.r;
+        c = p.c;
+        if (lvl < q.n_levels) {
+            const int kp = 2 * (r % 2) + (c % 2);
+            C = a.nin + qt_node(q, lvl + 1, r / 2, c / 2);
+            ms = C + (NP_MSG + ID_STRIDE * kp) * st;
+        }
+        lam = F.lam_R * level_scale<T>(lvl) * T(4);              // sigma_R / 2^l
+    }
+    T* dst = a.nout + n + (NP_MSG + ID_STRIDE * k) * st;
+    const T* N = a.nin + n;
+    // every load of the thread first: own pose, own old message, the sender's data
+    T xi[6], ov[ID_STRIDE], xs[6], W[21], u[6], ev[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) xi[m] = N[(NP_MU + m) * st];
+#pragma unroll
+    for (int m = 0; m < ID_STRIDE; ++m) ov[m] = N[(NP_MSG + ID_STRIDE * k + m) * st];
+    if (S) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            xs[m] = S[m * TILE_PX];
+            u[m] = S[(PL_U + m) * TILE_PX];
+            ev[m] = -S[(PL_ID + 21 + m) * TILE_PX];
+        }
+#pragma unroll
+        for (int m = 0; m < 21; ++m) W[m] = S[(PL_MP + m) * TILE_PX] - S[(PL_ID + m) * TILE_PX];
+    } else if (C) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            xs[m] = C[(NP_MU + m) * st];
+            u[m] = T(0);
+            ev[m] = -ms[(21 + m) * st];
+        }
+#pragma unroll
+        for (int m = 0; m < 21; ++m) W[m] = C[(NP_M + m) * st] - ms[m * st];
+    } else {
+#pragma unroll 1
+        for (int m = 0; m < ID_STRIDE; ++m) dst[m * st] = T(0);
+        return;
+    }
+    T R[9], t[3];
+    se3_exp(xi, R, t);
+    unsigned flags = 0;
+    T rb[6], L[21], e[6];
+    identity_residual(R, t, xs, rb);
+    identity_message(W, u, ev, rb, lam, L, e, &flags);
+    const T beta = F.beta, omb = T(1) - F.beta;
+#pragma unroll
+    for (int m = 0; m < 21; ++m) dst[m * st] = omb * L[m] + beta * ov[m];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) dst[(21 + m) * st] = omb * e[m] + beta * ov[21 + m];
+    if (flags) atomicOr(&a.sc->flags, flags);
+}
+
+// One thread per node: belief = pose prior (sigma_P / 2^l) plus the five damped
+// messages k_qt_node_msgs left in the output slots (summed in slot order), belief
+// solve, Exp/Log update, and eta <- eta - Lambda tau on every slot in place.
+template <typename T>
+__global__ void __launch_bounds__(128) k_qt_node_belief(const QtArgs<T> a) {
+    const QtGeom& q = a.q;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= q.n_nodes) return;
+    const Factors<T>& F = a.f;
+    const size_t st = q.stride;
+    const NodePos p = node_pos(q, n);
     const T* N = a.nin + n;
     T* O = a.nout + n;
     T xi[6], R[9], t[3];
 #pragma unroll
     for (int k = 0; k < 6; ++k) xi[k] = N[(NP_MU + k) * st];
     se3_exp(xi, R, t);
-    T scale_l = T(1);
-    for (int k = 0; k < lvl - 1; ++k) scale_l *= T(4);          // 4^(l-1)
-    const T lamP = F.lam_P * scale_l * T(4);                    // sigma_P / 2^l
+    const T lamP = F.lam_P * level_scale<T>(p.lvl) * T(4);     // sigma_P / 2^l
     T Mb[21], eb[6];
 #pragma unroll
     for (int k = 0; k < 21; ++k) Mb[k] = T(0);
@@ -374,85 +521,15 @@ __global__ void __launch_bounds__(128, 6) k_qt_nodes(const QtArgs<T> a) {
         Mb[pidx(k, k)] = lamP;
         eb[k] = -lamP * xi[k];
     }
-    unsigned flags = 0;
-    const T beta = F.beta, omb = T(1) - F.beta;
-    const T zero6[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-#pragma unroll 1
+#pragma unroll
     for (int k = 0; k < 5; ++k) {
-        T xs[6], W[21], u[6], ev[6], lam;
-        bool has;
-        if (k < 4) {
-            const int rc = 2 * r + k / 2, cc = 2 * c + k % 2;
-            lam = F.lam_R * scale_l;                             // sigma_R / 2^(l-1)
-            if (lvl == 1) {
-                has = rc < g.H && cc < g.W;
-                if (has) {
-                    const T* S = a.in + state_index(cc, rc, g.tiles_x);
+        const T* mk = O + (NP_MSG + ID_STRIDE * k) * st;
 #pragma unroll
-                    for (int m = 0; m < 6; ++m) {
-                        xs[m] = S[m * TILE_PX];
-                        u[m] = S[(PL_U + m) * TILE_PX];
-                        ev[m] = -S[(PL_ID + 21 + m) * TILE_PX];
-                    }
+        for (int m = 0; m < 21; ++m) Mb[m] += mk[m * st];
 #pragma unroll
-                    for (int m = 0; m < 21; ++m) W[m] = S[(PL_MP + m) * TILE_PX] - S[(PL_ID + m) * TILE_PX];
-                }
-            } else {
-                has = rc < q.h[lvl - 2] && cc < q.w[lvl - 2];
-                if (has) {
-                    const T* C = a.nin + qt_node(q, lvl - 1, rc, cc);
-                    const T* mp = C + (NP_MSG + ID_STRIDE * NP_PARENT) * st;
-#pragma unroll
-                    for (int m = 0; m < 6; ++m) {
-                        xs[m] = C[(NP_MU + m) * st];
-                        u[m] = T(0);
-                        ev[m] = -mp[(21 + m) * st];
-                    }
-#pragma unroll
-                    for (int m = 0; m < 21; ++m) W[m] = C[(NP_M + m) * st] - mp[m * st];
-                }
-            }
-        } else {
-            has = lvl < q.n_levels;
-            lam = F.lam_R * scale_l * T(4);                      // sigma_R / 2^l
-            if (has) {
-                const int kp = 2 * (r % 2) + (c % 2);
-                const T* P = a.nin + qt_node(q, lvl + 1, r / 2, c / 2);
-                const T* mk = P + (NP_MSG + ID_STRIDE * kp) * st;
-#pragma unroll
-                for (int m = 0; m < 6; ++m) {
-                    xs[m] = P[(NP_MU + m) * st];
-                    u[m] = T(0);
-                    ev[m] = -mk[(21 + m) * st];
-                }
-#pragma unroll
-                for (int m = 0; m < 21; ++m) W[m] = P[(NP_M + m) * st] - mk[m * st];
-            }
-        }
-        const T* old = N + (NP_MSG + ID_STRIDE * k) * st;
-        T* dst = O + (NP_MSG + ID_STRIDE * k) * st;
-        if (!has) {
-#pragma unroll 1
-            for (int m = 0; m < ID_STRIDE; ++m) dst[m * st] = T(0);
-            continue;
-        }
-        T rb[6], L[21], e[6];
-        identity_residual(R, t, xs, rb);
-        identity_message(W, u, ev, rb, lam, L, e, &flags);
-#pragma unroll
-        for (int m = 0; m < 21; ++m) {
-            const T l = omb * L[m] + beta * old[m * st];
-            Mb[m] += l;
-            dst[m * st] = l;
-        }
-#pragma unroll
-        for (int m = 0; m < 6; ++m) {
-            const T ee = omb * e[m] + beta * old[(21 + m) * st];
-            eb[m] += ee;
-            dst[(21 + m) * st] = ee;
-        }
+        for (int m = 0; m < 6; ++m) eb[m] += mk[(21 + m) * st];
     }
-    // belief solve and update
+    unsigned flags = 0;
     T tau[6], L[21], idg[6];
 #pragma unroll
     for (int k = 0; k < 21; ++k) L[k] = Mb[k];
@@ -480,7 +557,6 @@ __global__ void __launch_bounds__(128, 6) k_qt_nodes(const QtArgs<T> a) {
     }
 #pragma unroll
     for (int k = 0; k < 21; ++k) O[(NP_M + k) * st] = Mb[k];
-    // eta <- eta - Lambda tau on every stored message (read back from this thread's stores)
 #pragma unroll 1
     for (int k = 0; k < 5; ++k) {
         T* dk = O + (NP_MSG + ID_STRIDE * k) * st;
