@@ -34,6 +34,9 @@ W_IMG, H_IMG = 640, 480
 METRIC = "Mpixel*GBP-sweeps/s at 640x480"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_640x480_traffic.json")
+TRAFFIC_FILE_QT = os.path.join(ROOT, "profiles", "quadtree_640x480_traffic.json")
+SWEEP_SOURCES = ("pv_kernels.cuh", "pv_math.cuh", "pv_batch.cuh")
+QT_SOURCES = ("pv_quadtree.cuh", "pv_kernels.cuh", "pv_math.cuh")
 STATE_PLANES, INPUT_PLANES = 151, 6
 # algorithmic bytes per pixel per sweep (FP32): every state plane read once and
 # written once, plus the six input planes (I_s, I_t, g_x, g_y, m_x, m_y) read once
@@ -128,22 +131,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernel_source_hash():
+def kernel_source_hash(files=SWEEP_SOURCES):
     h = hashlib.sha256()
-    for f in ("pv_kernels.cuh", "pv_math.cuh", "pv_batch.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2606_03989_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
-    """ncu DRAM bytes per sweep launch, if taken on the current kernel source."""
+def measured_traffic(path=TRAFFIC_FILE, files=SWEEP_SOURCES):
+    """ncu DRAM bytes per sweep, if taken on the current kernel source."""
     try:
-        with open(TRAFFIC_FILE) as fh:
+        with open(path) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_source_hash") != kernel_source_hash():
+    if rec.get("kernel_source_hash") != kernel_source_hash(files):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -412,7 +415,9 @@ def run_quadtree(args):
                                "keyframe every 10 frames, quadtree identity factors (%d node levels, %d nodes)"
                                % (args.sweeps, 10, n_nodes), "sweeps_per_frame": args.sweeps},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_qt_pixels<float> + k_qt_node_msgs<float> + k_qt_node_belief<float>", "peak_source": peak_kind,
+                     "traffic": measured_traffic(TRAFFIC_FILE_QT, QT_SOURCES),
+                     "kernel": "k_qt_pixels<float> + k_qt_node_msgs<float> + k_qt_node_belief<float>",
+                     "peak_source": peak_kind,
                      "bytes_per_launch": bytes_sweep, "sweep_ms": q["sweep_ms"]},
         "grid_same_frames": {"value": px * args.sweeps * args.steps / (out[pv.TOPOLOGY_GRID]["ms"] * 1e-3) / 1e6,
                              "sweep_ms": out[pv.TOPOLOGY_GRID]["sweep_ms"]},
