@@ -712,13 +712,16 @@ def _se3_log(T):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 100; 10 for the adjoint workload, whose steps take seconds)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--sweeps", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="realistic",
                     choices=["realistic", "batched", "adjoint", "ablation", "quadtree"])
     args = ap.parse_args(argv)
+    if args.steps is None:
+        args.steps = 10 if args.workload == "adjoint" else 100
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":

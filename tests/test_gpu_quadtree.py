@@ -1,8 +1,9 @@
 """Quadtree identity topology on the GPU (topology = PIXVOD_TOPOLOGY_QUADTREE)
 against the quadtree oracle (oracle/quadtree.py, pinned in
 test_oracle_quadtree.py): the pixel state after 1 and 3 synchronous sweeps from
-the keyframe reset, on 16x12, a ragged 33x17 and 64x48 (six node levels); the
-node states of every level; checkpoints of quadtree handles."""
+the keyframe reset, on 16x12, a ragged 33x17 and 64x48 (six node levels), and
+after 2 sweeps at 640x480; the node states of every level; checkpoints of
+quadtree handles."""
 import numpy as np
 import pytest
 
@@ -90,6 +91,29 @@ def test_fp64_node_states_match_the_quadtree_oracle(size):
         assert err < 1e-8, (k, err)
     # the root has no parent
     assert np.all(got["msg"][-1, qt.NODE_PARENT] == 0.0)
+
+
+def test_full_size_two_sweeps_fp64():
+    """640x480, the benchmark size: 10 node levels, 102,409 nodes, and every
+    thread range of the node-message launch many blocks deep. Two FP64 sweeps
+    from the keyframe reset against the oracle at every pixel and every node."""
+    seq = synth.realistic(2, 2)
+    st, p = oracle_pair(seq, 2)
+    trk = run_pair(seq, 64, 2)
+    assert trk.status() == 0
+    view = trk.state()
+    err = field_errors(compressed_from_view(view), compressed_from_oracle(st.pixels, 1 / p.sigma_P ** 2))
+    assert max(err["P"], err["M_p"], err["s"], err["id"], err["nm"]) < 1e-8, err
+    assert err["mu_abs"] < 1e-8, err
+    ora = oracle_nodes(st)
+    n = ora["mu"].shape[0]
+    assert n == 102409 and view.nodes.shape == (162, n)
+    nd = view.nodes.T
+    assert np.abs(nd[:, 0:6] - ora["mu"]).max() < 1e-8
+    assert np.abs(nd[:, 6:27] - ora["M"]).max() / np.abs(ora["M"]).max() < 1e-8
+    msg = nd[:, 27:162].reshape(n, qt.NODE_SLOTS, 27)
+    assert np.abs(msg - ora["msg"]).max() / np.abs(ora["msg"]).max() < 1e-8
+    assert np.abs(trk.pose() - gbp.pose_estimate(st.pixels.mu)).max() < 1e-10
 
 
 @pytest.mark.parametrize("precision", [32, 64])
