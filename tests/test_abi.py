@@ -73,6 +73,23 @@ def test_workspace_and_validation_without_a_gpu(pv):
     assert pv.lib.pixvod_destroy(None) == pv.OK
 
 
+def test_quadtree_workspace_holds_two_node_buffers(pv):
+    """A quadtree handle adds two ping-pong buffers of 162 node planes; the node
+    count follows the level shapes of the quadtree oracle (ceil halving down to one
+    node): 102,409 nodes in 10 levels at 640x480."""
+    from oracle import quadtree as qt
+    for (w, h) in ((640, 480), (33, 17), (2, 9)):
+        K = pv.intrinsics(525, 525, (w - 1) / 2, (h - 1) / 2, w, h)
+        grid = pv.workspace_bytes(K, pv.params_default())
+        quad = pv.workspace_bytes(K, pv.params(topology=pv.TOPOLOGY_QUADTREE))
+        n = sum(a * b for a, b in qt.level_shapes(h, w))
+        stride = (n + 63) // 64 * 64
+        assert quad - grid >= 2 * 162 * stride * 4
+        assert quad - grid < 2 * 162 * stride * 4 + 2 * 4096
+    assert sum(a * b for a, b in qt.level_shapes(480, 640)) == 102409
+    assert len(qt.level_shapes(480, 640)) == 10
+
+
 def test_binding_fails_loudly_without_the_library(tmp_path):
     """Importing the binding from a copy with no built library raises."""
     import shutil

@@ -51,3 +51,30 @@ def test_checkpoint_blob_decodes_to_the_same_fields(tiny_seq):
         np.testing.assert_array_equal(view.normal_messages, cr["nm"])
         np.testing.assert_allclose(view.P, cr["P"], rtol=1e-15, atol=0)
         np.testing.assert_array_equal(view.inputs[1], np.asarray(win.I_t, np.float32 if prec == 32 else np.float64))
+
+
+def test_quadtree_checkpoint_node_section_decodes(tiny_seq):
+    """Header words 12..14 (node count, node planes, byte offset) locate the node
+    section a quadtree handle appends after the scalars; grid blobs have none."""
+    pv = pytest.importorskip("paper_2606_03989_gb300")
+    from paper_2606_03989_gb300 import build
+    build.build()
+    K = oracle_intrinsics(tiny_seq.cam)
+    p = oracle_params(sigma_P=tiny_seq.sigma_P)
+    win = oracle_window(tiny_seq, K)
+    c = synthetic_state(48, 64, p, seed=3)
+    from oracle import quadtree as qt
+    n = sum(h * w for h, w in qt.level_shapes(48, 64))
+    rng = np.random.default_rng(5)
+    for prec in (64, 32):
+        dt = np.float64 if prec == 64 else np.float32
+        grid = blob_from_compressed(rounded(c, prec), win, prec)
+        assert pv.parse_state(grid).nodes is None
+        nodes = rng.normal(size=(162, n)).astype(dt)
+        hd = np.frombuffer(grid, "<i8", count=32).copy()
+        hd[12:15] = [n, 162, len(grid)]
+        blob = hd.tobytes() + grid[256:] + nodes.tobytes()
+        view = pv.parse_state(blob)
+        np.testing.assert_array_equal(view.nodes, nodes.astype(np.float64))
+        np.testing.assert_array_equal(view.node_pose, nodes[0:6].T.astype(np.float64))
+        np.testing.assert_array_equal(view.mu, rounded(c, prec)["mu"])
