@@ -661,7 +661,7 @@ def run_ablation(args):
 
     curves = {name: {str(sw): track_all(frames[name], sw) for sw in (5, 10, 20, 40)} for name in frames}
     curves["default_quadtree"] = {str(sw): track_all(frames["default"], sw, params_qt) for sw in (5, 10, 20, 40)}
-    basin = {"reset_depth": [], "gt_depth": [], "quadtree_reset_depth": []}   # (load_state: grid only)
+    basin = {"reset_depth": [], "gt_depth": [], "quadtree_reset_depth": [], "quadtree_gt_depth": []}
     for key in basin:
         init = "gt_depth" if key.endswith("gt_depth") else "reset_depth"
         prm = params_qt if key.startswith("quadtree") else params
