@@ -1,9 +1,9 @@
 """Quadtree identity topology on the GPU (topology = PIXVOD_TOPOLOGY_QUADTREE)
 against the quadtree oracle (oracle/quadtree.py, pinned in
 test_oracle_quadtree.py): the pixel state after 1 and 3 synchronous sweeps from
-the keyframe reset, on 16x12, a ragged 33x17 and 64x48 (six node levels), and
-after 2 sweeps at 640x480; the node states of every level; checkpoints of
-quadtree handles."""
+the keyframe reset, on 16x12, a ragged 33x17 and 64x48 (six node levels), on
+degenerate trees (one level; one node column or row), and after 2 sweeps at
+640x480; the node states of every level; checkpoints of quadtree handles."""
 import numpy as np
 import pytest
 
@@ -91,6 +91,27 @@ def test_fp64_node_states_match_the_quadtree_oracle(size):
         assert err < 1e-8, (k, err)
     # the root has no parent
     assert np.all(got["msg"][-1, qt.NODE_PARENT] == 0.0)
+
+
+@pytest.mark.parametrize("size", [(2, 2), (2, 9), (9, 2), (5, 3)])
+def test_degenerate_trees_fp64(size):
+    """Trees of one level (2x2: the level-1 node is the root), one node column or
+    row, and odd sides at every level: one FP64 sweep from the reset against the
+    oracle, pixels and nodes."""
+    seq = synth.realistic(7, 2, *size)
+    st, p = oracle_pair(seq, 1)
+    trk = run_pair(seq, 64, 1)
+    assert trk.status() == 0
+    view = trk.state()
+    err = field_errors(compressed_from_view(view), compressed_from_oracle(st.pixels, 1 / p.sigma_P ** 2))
+    assert max(err["P"], err["M_p"], err["s"], err["id"], err["nm"]) < 1e-9, err
+    assert err["mu_abs"] < 1e-9, err
+    ora = oracle_nodes(st)
+    n = ora["mu"].shape[0]
+    nd = view.nodes.T
+    assert np.abs(nd[:, 0:6] - ora["mu"]).max() < 1e-9
+    for got, ref in ((nd[:, 6:27], ora["M"]), (nd[:, 27:162].reshape(n, qt.NODE_SLOTS, 27), ora["msg"])):
+        assert np.abs(got - ref).max() <= 1e-9 * max(np.abs(ref).max(), 1.0)
 
 
 def test_full_size_two_sweeps_fp64():
