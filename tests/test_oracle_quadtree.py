@@ -63,9 +63,37 @@ def test_level_shapes():
     assert qt.level_shapes(48, 64) == [(24, 32), (12, 16), (6, 8), (3, 4), (2, 2), (1, 1)]
     assert qt.level_shapes(17, 33) == [(9, 17), (5, 9), (3, 5), (2, 3), (1, 2), (1, 1)]
     assert qt.level_shapes(1, 1) == []
-    p = gbp.Params()
-    assert qt.sigma_R_between(p, 1) == p.sigma_R and qt.sigma_R_between(p, 3) == p.sigma_R / 4
-    assert qt.sigma_P_at(p, 2) == p.sigma_P / 4
+
+
+def test_level_strengths_match_the_printed_geometric_means():
+    """App. E.2 prints the geometric means of the per-layer strengths of the
+    hierarchy the paper runs on its 128 x 128 images (sigma_R = 3.536e-5,
+    sigma_P = 8.839e-2 from the Sec. 4.2 leaf values). A 128 x 128 tree has eight
+    layers (the pixels and seven node levels). Layer l's sigma_P is that of its
+    own prior; its sigma_R is that of the factor joining it to its parent, and
+    the root's is the value the halving rule gives the layer above the last
+    factor (it has no parent, the mean still counts it). A schedule that halves
+    from the wrong layer (sigma_R / 2^l between levels l - 1 and l) or at another
+    rate misses the printed values by a factor of 1.4 or more."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")) as fh:
+        gold = json.load(fh)
+    leaf = gold["sec4_2_leaf"]
+    p = gbp.Params(sigma_P=leaf["sigma_P"], sigma_R=leaf["sigma_R"])
+    layers = len(qt.level_shapes(128, 128)) + 1
+    assert layers == 8
+    s_P = [qt.sigma_P_at(p, l) for l in range(layers)]
+    s_R = [qt.sigma_R_between(p, l + 1) for l in range(layers)]
+    gmean = lambda xs: float(np.exp(np.mean(np.log(xs))))  # noqa: E731
+    # the paper prints four significant digits
+    assert gmean(s_P) == pytest.approx(gold["appE2_geometric_mean"]["sigma_P"], rel=6e-4)
+    assert gmean(s_R) == pytest.approx(gold["appE2_geometric_mean"]["sigma_R"], rel=6e-4)
+    # consecutive layers differ by the Sec. 4.2 factor
+    for a, b in zip(s_P[1:], s_P[:-1]):
+        assert a / b == pytest.approx(gold["sec4_2_level_factor"])
+    # only the seven factors below the root exist in the oracle's tree
+    assert len(s_R[:-1]) == len(qt.level_shapes(128, 128))
 
 
 @pytest.mark.parametrize("shape", [(8, 8), (6, 7)])
