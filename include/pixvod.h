@@ -180,7 +180,10 @@ pixvod_status pixvod_get_depth(pixvod_handle* h, float* d_depth);
 pixvod_status pixvod_get_inv_depth(pixvod_handle* h, float* d_inv_depth);
 
 /* Sticky device flags (PIXVOD_FLAG_*). Synchronises the stream. Returns
- * ENUMERIC when any flag is set, OK otherwise. */
+ * ETIMEOUT when PIXVOD_FLAG_TIMEOUT is set (a bounded wait gave up: the sweep
+ * that set it stopped early, so the state is not a sweep result and should be
+ * reloaded from a checkpoint or re-anchored), else ENUMERIC when any other flag
+ * is set, OK otherwise. */
 pixvod_status pixvod_get_status(pixvod_handle* h, uint32_t* flags);
 
 /* Checkpoint of the full sweep state: a 256-byte header, the state planes, the
@@ -326,8 +329,8 @@ pixvod_status pixvod_batch_track(pixvod_batch* b, int32_t n_iters);
 /* xi_est of every sequence, 6 doubles per sequence into host memory. Synchronises. */
 pixvod_status pixvod_batch_get_poses(pixvod_batch* b, double* xi);
 
-/* OR of every sequence's device flags and the batch's own. Synchronises; ENUMERIC
- * when any flag is set. */
+/* OR of every sequence's device flags and the batch's own. Synchronises; ETIMEOUT
+ * when PIXVOD_FLAG_TIMEOUT is set, else ENUMERIC when any flag is set. */
 pixvod_status pixvod_batch_get_status(pixvod_batch* b, uint32_t* flags);
 
 /* Checkpoint of sequence i, in the pixvod_save_state format. Synchronises. */
@@ -351,14 +354,32 @@ pixvod_status pixvod_batch_autotune(pixvod_batch* b, int32_t n_iters, int32_t re
 /* Kernels the batch has launched since creation. */
 pixvod_status pixvod_batch_launch_count(pixvod_batch* b, int64_t* out);
 
+/* Bounded waits of the persistent schedule (diagnostics and tests of the failure
+ * path). The grid barrier between sweeps polls an arrival counter; after `polls`
+ * polls (each followed by a ~64 ns sleep) a block gives up, sets
+ * PIXVOD_FLAG_TIMEOUT and leaves the launch, and the batch's status becomes
+ * ETIMEOUT. polls = 0 restores the default of 2^24 (about a second). EINVAL if
+ * polls < 0. */
+pixvod_status pixvod_batch_set_wait_limit(pixvod_batch* b, int64_t polls);
+
+/* Test hook for the failure path: while `on` is nonzero, every persistent launch
+ * starts its grid barrier's arrival counter at 2^24 instead of 0, above any grid
+ * size, so no arrival is ever counted as the last one and every block's bounded
+ * wait runs out (nothing faults and nothing hangs; the blocks return). The
+ * frame's state is then invalid.
+ * Plain and batched schedules have no grid barrier and are unaffected. */
+pixvod_status pixvod_batch_inject_barrier_fault(pixvod_batch* b, int32_t on);
+
 /* Pose average without any device allocation. The paper has no counterpart: this
  * is a library convenience for callers that cannot allocate device memory, such
  * as code that runs while a CUDA stream is being captured, a real-time loop that
  * forbids allocation after start-up, or a plugin whose host framework owns all
- * device memory and offers it no workspace. It computes the same seven means as
- * the tracker's own reduction (xi_est[0..5] and the mean log-depth, in row order
- * with double accumulation) from caller-provided planes, using scratch held in a
- * static device array of the library instead of a workspace.
+ * device memory and offers it no workspace. It computes the seven means the
+ * tracker's own reduction computes (xi_est[0..5] and the mean log-depth), equal to
+ * them up to FP64 rounding: here rows are summed in row order, the tracker sums
+ * 32 x 4 tiles in tile order, both with double accumulation. The inputs are
+ * caller-provided planes; the scratch is a static device array of the library
+ * instead of a workspace.
  *   d_mu: 7 float32 planes (xi_0..xi_5, log-depth) of height rows of `pitch`
  *         elements, `plane_stride` elements apart (the checkpoint plane layout);
  *   d_out: 7 doubles of device memory (the means); stream: a cudaStream_t.

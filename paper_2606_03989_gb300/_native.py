@@ -102,6 +102,8 @@ def _load():
         "pixvod_batch_get_schedule": (S, [H, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "pixvod_batch_autotune": (S, [H, I32, I32, P]),
         "pixvod_batch_launch_count": (S, [H, ctypes.POINTER(I64)]),
+        "pixvod_batch_set_wait_limit": (S, [H, I64]),
+        "pixvod_batch_inject_barrier_fault": (S, [H, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -376,7 +376,7 @@ pixvod_status run_sweeps(pixvod_handle* h, int n) {
             s = launch_qt_sweep<T>(h);
         } else {
             pv::k_sweeps<T><<<n_tiles, sweep_block(), pv::sweep_smem_bytes<T>(), h->stream>>>(
-                desc_ptr<T>(h), nullptr, n_tiles, 1, h->cur, pv::GridSync{nullptr, nullptr, nullptr});
+                desc_ptr<T>(h), nullptr, n_tiles, 1, h->cur, pv::GridSync{nullptr, nullptr, nullptr, 0});
             s = launched(h);
         }
         if (prof) {
@@ -548,7 +548,7 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
         if (c + len <= first) break;
         for (int j = 1; j <= len; ++j) {
             pv::k_sweeps<T><<<n_tiles, sweep_block(), pv::sweep_smem_bytes<T>(), st>>>(
-                ddesc + (c + j - 1), nullptr, n_tiles, 1, 0, pv::GridSync{nullptr, nullptr, nullptr});
+                ddesc + (c + j - 1), nullptr, n_tiles, 1, 0, pv::GridSync{nullptr, nullptr, nullptr, 0});
             if ((s = launched(h)) != PIXVOD_OK) return s;
         }
         for (int j = len; j >= 1 && c + j > first; --j) {
@@ -582,6 +582,13 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
 }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// status of a set of sticky device flags: a timed-out wait first (the state it
+// left is not a sweep result), then numerical flags
+pixvod_status flags_status(uint32_t flags) {
+    if (flags & pv::FLAG_TIMEOUT) return PIXVOD_ETIMEOUT;
+    return flags ? PIXVOD_ENUMERIC : PIXVOD_OK;
+}
 
 constexpr int64_t kMagic = 0x50495856;
 constexpr int kHeaderBytes = 256;
@@ -805,7 +812,7 @@ pixvod_status pixvod_get_status(pixvod_handle* h, uint32_t* flags) {
         cudaMemcpyAsync(flags, &scalars(h)->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
     if (s != PIXVOD_OK) return s;
     if ((s = cuda_status(cudaStreamSynchronize(h->stream))) != PIXVOD_OK) return s;
-    return *flags ? PIXVOD_ENUMERIC : PIXVOD_OK;
+    return flags_status(*flags);
 }
 
 pixvod_status pixvod_state_size(pixvod_handle* h, size_t* bytes) {
@@ -1006,6 +1013,8 @@ struct pixvod_batch {
     int blocks_per_sm;
     int max_blocks_per_sm;
     int num_sms;
+    long long wait_limit;   // polls of the grid barrier before it gives up
+    bool barrier_fault;     // test hook: arrival counter starts at 1 (pixvod_batch_inject_barrier_fault)
     bool inputs_set;
     std::vector<const float*> frames, normals;
     int64_t frame_index;
@@ -1076,14 +1085,20 @@ pixvod_status batch_sweeps(pixvod_batch* b, int n_iters, int schedule) {
     if (schedule == PIXVOD_SCHED_BATCHED) {
         for (int it = 0; it < n_iters; ++it) {
             pv::k_sweeps<T><<<b->n_work, sweep_block(), pv::sweep_smem_bytes<T>(), b->stream>>>(
-                descs<T>(b), works(b), b->n_work, 1, cur, pv::GridSync{nullptr, nullptr, nullptr});
+                descs<T>(b), works(b), b->n_work, 1, cur, pv::GridSync{nullptr, nullptr, nullptr, 0});
             if ((s = batch_launched(b)) != PIXVOD_OK) return s;
             cur ^= 1;
         }
     } else {
         unsigned* sy = batch_sync(b);
         if ((s = cuda_status(cudaMemsetAsync(sy, 0, sizeof(unsigned), b->stream))) != PIXVOD_OK) return s;
-        pv::GridSync gs{sy, sy + 1, sy + 2};
+        // injected fault: a counter that starts at 2^24 (its high byte set), above
+        // any grid size, never reaches the grid size at an arrival, so every block's
+        // bounded wait runs out
+        if (b->barrier_fault &&
+            (s = cuda_status(cudaMemsetAsync(reinterpret_cast<char*>(sy) + 3, 1, 1, b->stream))) != PIXVOD_OK)
+            return s;
+        pv::GridSync gs{sy, sy + 1, sy + 2, b->wait_limit};
         int grid = b->blocks_per_sm * b->num_sms;
         if (grid > b->n_work) grid = b->n_work;
         const pv::SeqDesc<T>* d = descs<T>(b);
@@ -1240,6 +1255,8 @@ pixvod_status pixvod_batch_create(int32_t n, const pixvod_intrinsics* K, const p
     b->off_sync = B.off_sync;
     b->n_work = B.n_work;
     b->schedule = PIXVOD_SCHED_PERSISTENT;
+    b->wait_limit = pv::GRID_SYNC_DEFAULT_LIMIT;
+    b->barrier_fault = false;
     b->inputs_set = false;
     b->frames.assign(n, nullptr);
     b->normals.assign(n, nullptr);
@@ -1364,7 +1381,7 @@ pixvod_status pixvod_batch_get_status(pixvod_batch* b, uint32_t* flags) {
     uint32_t all = 0;
     for (uint32_t x : f) all |= x;
     *flags = all;
-    return all ? PIXVOD_ENUMERIC : PIXVOD_OK;
+    return flags_status(all);
 }
 
 pixvod_status pixvod_batch_state_size(pixvod_batch* b, int32_t i, size_t* bytes) {
@@ -1401,6 +1418,18 @@ pixvod_status pixvod_batch_autotune(pixvod_batch* b, int32_t n_iters, int32_t re
     if (!b->inputs_set || b->frame_index != 1) return PIXVOD_ESTATE;
     return b->p.precision == 64 ? batch_autotune_impl<double>(b, n_iters, reps, times_ms)
                                 : batch_autotune_impl<float>(b, n_iters, reps, times_ms);
+}
+
+pixvod_status pixvod_batch_set_wait_limit(pixvod_batch* b, int64_t polls) {
+    if (!b || polls < 0) return PIXVOD_EINVAL;
+    b->wait_limit = polls == 0 ? pv::GRID_SYNC_DEFAULT_LIMIT : (long long)polls;
+    return PIXVOD_OK;
+}
+
+pixvod_status pixvod_batch_inject_barrier_fault(pixvod_batch* b, int32_t on) {
+    if (!b) return PIXVOD_EINVAL;
+    b->barrier_fault = on != 0;
+    return PIXVOD_OK;
 }
 
 pixvod_status pixvod_batch_launch_count(pixvod_batch* b, int64_t* out) {

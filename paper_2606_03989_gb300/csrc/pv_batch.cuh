@@ -48,11 +48,14 @@ __device__ __forceinline__ SweepArgs<T> seq_args(const SeqDesc<T>& d, int cur) {
 }
 
 // Grid-wide barrier for a cooperative launch (all blocks resident). The wait is
-// bounded: on expiry the block sets FLAG_TIMEOUT in *flags and gets false.
+// bounded: after `limit` polls (each followed by a short sleep) the block sets
+// FLAG_TIMEOUT in *flags and gets false.
+constexpr long long GRID_SYNC_DEFAULT_LIMIT = 1ll << 24;
 struct GridSync {
     unsigned* count;
     unsigned* gen;
     unsigned* flags;
+    long long limit;
 };
 
 __device__ __forceinline__ bool grid_sync(const GridSync& gs) {
@@ -68,9 +71,9 @@ __device__ __forceinline__ bool grid_sync(const GridSync& gs) {
             __threadfence();
             atomicAdd(gs.gen, 1u);
         } else {
-            long spins = 0;
+            long long spins = 0;
             while (*gen == g0) {
-                if (++spins > (1l << 24)) {
+                if (++spins > gs.limit) {
                     ok = 0;
                     atomicOr(gs.flags, FLAG_TIMEOUT);
                     break;
@@ -113,7 +116,10 @@ __global__ void __launch_bounds__(SWEEP_THREADS, 4) k_sweeps(const SeqDesc<T>* _
         for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
             const Work wk = work ? work[w] : Work{0, w};
             const SweepArgs<T> a = seq_args(seqs[wk.seq], cur);
-            sweep_tile(a, wk.tile % a.g.tiles_x, wk.tile / a.g.tiles_x, msg, &bar, parity);
+            // a tile whose bulk copy never arrived ends the block's work for the
+            // launch: the mbarrier's phase no longer matches `parity`, and the copy
+            // may still be writing `msg`
+            if (!sweep_tile(a, wk.tile % a.g.tiles_x, wk.tile / a.g.tiles_x, msg, &bar, parity)) return;
             parity ^= 1u;
             if (n_iters > 1) asm volatile("fence.proxy.async.global;" ::: "memory");
             __syncthreads();

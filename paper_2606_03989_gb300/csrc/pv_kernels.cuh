@@ -602,9 +602,12 @@ __device__ __forceinline__ void bulk_copy_s2g(void* dst, const void* src, unsign
 // thread of the block must call it). The block must have initialised `bar` (one
 // arrival); `parity` is the phase this tile's bulk copy completes. The caller
 // synchronises the block before reusing `msg` for another tile. The message
-// planes of pixels outside the image are copied through unchanged.
+// planes of pixels outside the image are copied through unchanged. Returns
+// false (to every thread) when the tile's bulk copy did not arrive within the
+// bounded wait: nothing of the tile was stored, FLAG_TIMEOUT is set, and the
+// block must take no further tile in this launch.
 template <typename T>
-__device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty, T* msg, uint64_t* bar,
+__device__ __forceinline__ bool sweep_tile(const SweepArgs<T>& a, int tx, int ty, T* msg, uint64_t* bar,
                                            unsigned parity) {
     const int tid = threadIdx.y * SWEEP_BX + threadIdx.x;
     const size_t tile = (size_t)ty * a.g.tiles_x + tx;
@@ -621,7 +624,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<T>& a, int tx, int ty
     // the bulk copy (async proxy): fence, then gather the block; a tile whose
     // messages never arrived is not stored
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (__syncthreads_and(ok) && tid == 0) bulk_copy_s2g(a.out + tile * TILE_WORDS + PL_ID * TILE_PX, msg, bytes);
+    const bool all_ok = __syncthreads_and(ok);
+    if (all_ok && tid == 0) bulk_copy_s2g(a.out + tile * TILE_WORDS + PL_ID * TILE_PX, msg, bytes);
+    return all_ok;
 }
 
 // ---------------------------------------------------------------------------

@@ -127,7 +127,7 @@ class Tracker:
     def status(self) -> int:
         flags = ctypes.c_uint32(0)
         st = nat.lib.pixvod_get_status(self._h, ctypes.byref(flags))
-        if st not in (nat.OK, nat.ENUMERIC):
+        if st not in (nat.OK, nat.ENUMERIC, nat.ETIMEOUT):
             nat.check(st, "pixvod_get_status")
         return flags.value
 
@@ -301,7 +301,7 @@ class Batch:
     def status(self) -> int:
         flags = ctypes.c_uint32(0)
         st = nat.lib.pixvod_batch_get_status(self._h, ctypes.byref(flags))
-        if st not in (nat.OK, nat.ENUMERIC):
+        if st not in (nat.OK, nat.ENUMERIC, nat.ETIMEOUT):
             nat.check(st, "pixvod_batch_get_status")
         return flags.value
 
@@ -336,3 +336,12 @@ class Batch:
         n = ctypes.c_int64(0)
         nat.check(nat.lib.pixvod_batch_launch_count(self._h, ctypes.byref(n)), "pixvod_batch_launch_count")
         return n.value
+
+    def set_wait_limit(self, polls: int):
+        """Polls of the persistent schedule's grid barrier before it gives up (0: default)."""
+        nat.check(nat.lib.pixvod_batch_set_wait_limit(self._h, int(polls)), "pixvod_batch_set_wait_limit")
+
+    def inject_barrier_fault(self, on: bool):
+        """Test hook: make every grid barrier of the persistent schedule time out."""
+        nat.check(nat.lib.pixvod_batch_inject_barrier_fault(self._h, 1 if on else 0),
+                  "pixvod_batch_inject_barrier_fault")

@@ -228,3 +228,44 @@ def run_oracle_pair(seq, K, p: Params, n_iters, record=()):
         if k in record:
             rec[k] = st
     return st, rec, win
+
+
+def oracle_track(seq, K: Intrinsics, p: Params, kf: int, n_frames=None, eps: float = 0.0, sweeps=None):
+    """The oracle tracker over frames 0..n_frames-1 of a sequence (frames scaled
+    by 1 + eps). Per frame: (xi_est, T_cam<-world, log-depth prior mean, mu,
+    valid-warp mask or None)."""
+    from oracle.tracker import Tracker
+    ora = Tracker(K, p, kf_interval=kf)
+    out = []
+    for k in range(seq.n_frames if n_frames is None else n_frames):
+        f = seq.frame(k).astype(np.float64) * (1.0 + eps)
+        xi = ora.track(f, seq.normals(k).astype(np.float64), n_iters=seq.sweeps if sweeps is None else sweeps)
+        out.append((xi.copy(), ora.pose_global(), ora.win.d_prior, ora.state.mu.copy(),
+                    ora.state.diag.get("valid")))
+    return ora, out
+
+
+def compare_tracks(gpu, ref, pert=None, label=""):
+    """Per-frame results of a GPU run, ``gpu`` = [(xi, T, d_prior, mu)], against the
+    oracle's ``ref``. The bar is the stated tolerance, or, when ``pert`` is given,
+    max(stated tolerance, 100 x the oracle's own response ``pert`` to a 1e-15
+    relative perturbation of the frames): a floor for the error any FP64
+    implementation's rounding produces on an iteration that amplifies it. Returns
+    the largest (pose, inverse-depth) errors."""
+    worst = (0.0, 0.0)
+    if pert is None:
+        pert = ref
+    for k, ((xi, T, dp, mu), (xi_o, T_o, dp_o, mu_o, valid), pk) in enumerate(zip(gpu, ref, pert)):
+        sens_pose = np.abs(pk[0] - xi_o).max()
+        sens_inv = inv_depth_rel_err(pk[3][..., 6], mu_o[..., 6], valid)
+        e_pose = np.abs(xi - xi_o).max()
+        e_inv = inv_depth_rel_err(mu[..., 6], mu_o[..., 6], valid)
+        print("%s frame %d: pose %.1e (oracle sensitivity %.1e) inverse depth %.1e (sensitivity %.1e)"
+              % (label, k, e_pose, sens_pose, e_inv, sens_inv))
+        assert e_pose < max(1e-5, 100 * sens_pose), (label, k)
+        assert np.abs(T - T_o).max() < max(1e-5, 100 * sens_pose), (label, k)
+        # the prior mean is a mean log-depth: held like the inverse depths
+        assert abs(dp - dp_o) < max(1e-4, 100 * abs(pk[2] - dp_o)), (label, k, dp - dp_o)
+        assert e_inv < max(1e-4, 100 * sens_inv), (label, k)
+        worst = (max(worst[0], e_pose), max(worst[1], e_inv))
+    return worst

@@ -32,13 +32,15 @@ from oracle.tracker import Tracker as OracleTracker  # noqa: E402
 
 from helpers import (blob_from_compressed, compressed_from_oracle, compressed_from_view,  # noqa: E402
                      field_errors, inv_depth_rel_err, oracle_intrinsics, oracle_params,
-                     oracle_state_from_compressed, oracle_sweep_at, oracle_window, rounded,
-                     run_oracle_pair, synthetic_state)
+                     oracle_state_from_compressed, oracle_sweep_at, oracle_track, oracle_window,
+                     rounded, run_oracle_pair, synthetic_state)
 
 DEV = torch.device("cuda:0")
 # one-sweep tolerances: normwise relative error of P, M_p, s and the messages,
-# and |mu_gpu - mu_oracle| <= TOL_MU (1 + |tau|_inf) per pixel
-ONE_SWEEP = {64: (1e-9, 1e-9), 32: (2e-3, 2e-3)}
+# and |mu_gpu - mu_oracle| <= TOL_MU (1 + |tau|_inf) per pixel. FP32: measured up
+# to 7.5e-5 (fields) and 2e-4 (means) on the oracle states of the tiny pair and
+# the synthetic 640x480 state; the bars are about 4x that.
+ONE_SWEEP = {64: (1e-9, 1e-9), 32: (3e-4, 1e-3)}
 
 
 def cuda(x):
@@ -143,7 +145,8 @@ def test_large_image_one_sweep_and_run():
     p = oracle_params(sigma_P=seq.sigma_P)
     win = oracle_window(seq, K)
     c = synthetic_state(1536, 2048, p, seed=5, logz=np.log(seq.depth(0)))
-    one_sweep_check(seq.cam, p, c, win, 32, sample_pixels(1536, 2048, 60, 9))
+    err, dmu = one_sweep_check(seq.cam, p, c, win, 32, sample_pixels(1536, 2048, 60, 9))
+    print("\n2048x1536 one sweep (synthetic state), FP32: %s mu %.1e" % ({a: "%.1e" % b for a, b in err.items()}, dmu))
     trk = make_tracker(seq.cam, 32, seq.sigma_P)
     trk.track(cuda(seq.frame(0)), cuda(seq.normals(0)))
     trk.track(cuda(seq.frame(1)), n_iters=5)
@@ -192,14 +195,7 @@ def test_fp32_trajectory_error_against_fp64(tiny):
 
 
 def _oracle_track(seq, K, p, kf, eps=0.0):
-    ora = OracleTracker(K, p, kf_interval=kf)
-    out = []
-    for k in range(seq.n_frames):
-        f = seq.frame(k).astype(np.float64) * (1.0 + eps)
-        xi = ora.track(f, seq.normals(k).astype(np.float64), n_iters=seq.sweeps)
-        out.append((xi.copy(), ora.pose_global(), ora.win.d_prior, ora.state.mu.copy(),
-                    ora.state.diag.get("valid")))
-    return ora, out
+    return oracle_track(seq, K, p, kf, eps=eps)
 
 
 def test_ragged_multiframe_with_keyframes_matches_oracle_tracker():
@@ -238,7 +234,9 @@ def test_ragged_multiframe_with_keyframes_matches_oracle_tracker():
         ora4.track(seq.frame(k).astype(np.float64), seq.normals(k).astype(np.float64), n_iters=seq.sweeps)
     c4 = compressed_from_oracle(ora4.state, 1 / p.sigma_P ** 2)
     for prec in (64, 32):
-        one_sweep_check(seq.cam, p, c4, ora4.win, prec)
+        err, dmu = one_sweep_check(seq.cam, p, c4, ora4.win, prec)
+        print("\n70x45 one sweep in the second segment, FP%d: %s mu %.1e"
+              % (prec, {a: "%.1e" % b for a, b in err.items()}, dmu))
 
 
 def test_full_size_trajectory_fp64_on_dependency_cones():
@@ -438,3 +436,118 @@ def test_argument_errors(tiny):
     with pytest.raises(pv.PixvodError):
         trk.load_state(bytes(bad))
     assert trk.status() == 0
+
+
+# --------------------------------------------------------------------------
+# FP32 trajectories at the stated tolerance, on inputs where the iteration
+# contracts
+# --------------------------------------------------------------------------
+def _affine_inputs(seq, coef):
+    """An exactly bilinear target image and the matching source image
+    (synth.affine_pair), as the float32 frames the library receives."""
+    aff = synth.affine_pair(seq, coef=coef)
+    return (aff["I_s"].astype(np.float32), aff["I_t"].astype(np.float32),
+            aff["normal"].astype(np.float32))
+
+
+def test_fp32_trajectory_meets_stated_tolerance_on_a_contracting_input():
+    """On the exactly bilinear pair (64x48 tiny camera, paper sigmas, sigma_P =
+    0.1) the FP64 oracle's response to a 1e-7 relative perturbation of the state
+    at every sweep stays below 1e-8 after 50 sweeps, so the iteration contracts
+    and the float32 library is held to the stated tolerance: pose mean 1e-5,
+    inverse depth 1e-4 relative on valid pixels, after the 50 sweeps."""
+    seq = synth.tiny_pair(0)
+    f0, f1, nrm = _affine_inputs(seq, (0.3, 0.004, -0.003, 2e-5))
+    K = oracle_intrinsics(seq.cam)
+    p = oracle_params(sigma_P=seq.sigma_P)
+    win = gbp.make_window(K, f0.astype(np.float64), nrm.astype(np.float64), f1.astype(np.float64))
+    st = gbp.reset_state(win.shape, 0.0, p)
+    for _ in range(seq.sweeps):
+        st = gbp.sweep(win, st, p)
+    valid = st.diag["valid"]
+    for prec, tol_pose, tol_inv in ((64, 1e-9, 1e-8), (32, 1e-5, 1e-4)):
+        trk = make_tracker(seq.cam, prec, seq.sigma_P)
+        trk.track(cuda(f0), cuda(nrm))
+        trk.track(cuda(f1), n_iters=seq.sweeps)
+        view = trk.state()
+        dpose = np.abs(trk.pose() - gbp.pose_estimate(st.mu)).max()
+        dinv_all = np.abs(np.expm1(-(view.mu[..., 6] - st.mu[..., 6])))
+        dinv = inv_depth_rel_err(view.mu[..., 6], st.mu[..., 6], valid)
+        print("\nFP%d vs oracle, bilinear pair 64x48, %d sweeps: pose %.1e, inverse depth max %.1e "
+              "(all pixels: median %.1e p99 %.1e max %.1e)" % (prec, seq.sweeps, dpose, dinv, np.median(dinv_all),
+                                                                np.quantile(dinv_all, 0.99), dinv_all.max()))
+        assert trk.status() == 0
+        assert dpose < tol_pose, (prec, dpose)
+        assert dinv < tol_inv, (prec, dinv)
+
+
+def test_fp32_full_size_trajectory_meets_stated_tolerance_on_a_contracting_input():
+    """640x480 (the benchmark size), the realistic scene under an exactly bilinear
+    target image, 20 sweeps: FP32 and FP64 library states against the oracle on
+    the 41x41 dependency cones of sampled pixels (exact after 20 sweeps), and the
+    FP32 pose and every pixel's inverse depth against the FP64 library run (itself
+    held to the oracle), all at the stated tolerance."""
+    seq = synth.realistic(2, 2)
+    f0, f1, nrm = _affine_inputs(seq, (0.3, 0.004, -0.003, 2e-6))
+    K = oracle_intrinsics(seq.cam)
+    p = oracle_params(sigma_P=seq.sigma_P)
+    n = 20
+    runs = {}
+    for prec in (64, 32):
+        trk = make_tracker(seq.cam, prec, seq.sigma_P)
+        trk.track(cuda(f0), cuda(nrm))
+        trk.track(cuda(f1), n_iters=n)
+        assert trk.status() == 0
+        runs[prec] = (trk.pose(), trk.state())
+    d64 = runs[64][1].mu
+    d32 = runs[32][1].mu
+    xi_avg = d64[..., :6].reshape(-1, 6).mean(0)
+    assert np.abs(runs[64][0] - xi_avg).max() < 1e-12
+    dpose = np.abs(runs[32][0] - runs[64][0]).max()
+    dinv = np.abs(np.expm1(-(d32[..., 6] - d64[..., 6])))
+    print("\nFP32 vs FP64 library, bilinear 640x480, %d sweeps: pose %.1e, inverse depth median %.1e "
+          "p99 %.1e max %.1e" % (n, dpose, np.median(dinv), np.quantile(dinv, 0.99), dinv.max()))
+    assert dpose < 1e-5
+    assert dinv.max() < 1e-4
+    m_x, m_y = fac.normal_edge_measurements(nrm.astype(np.float64), K)
+    I_t = f1.astype(np.float64)
+    g_x, g_y = fac.image_gradient(I_t)
+    I_s = f0.astype(np.float64)
+    worst = {64: 0.0, 32: 0.0}
+    for (v, u) in sample_pixels(480, 640, 16, 4):
+        v0, v1, u0, u1 = max(v - n, 0), min(v + n + 1, 480), max(u - n, 0), min(u + n + 1, 640)
+        sub = gbp.Window(K, I_s[v0:v1, u0:u1], m_x[v0:v1, u0:u1 - 1], m_y[v0:v1 - 1, u0:u1], I_t, g_x, g_y,
+                         u0, v0, 0.0)
+        st = gbp.reset_state(sub.shape, 0.0, p)
+        for _ in range(n):
+            st = gbp.sweep(sub, st, p)
+        r, q = v - v0, u - u0
+        for prec, mu in ((64, d64), (32, d32)):
+            e_pose = np.abs(mu[v, u, :6] - st.mu[r, q, :6]).max()
+            e_inv = abs(np.expm1(-(mu[v, u, 6] - st.mu[r, q, 6])))
+            worst[prec] = max(worst[prec], e_pose, e_inv)
+            assert e_pose < 1e-5 and e_inv < 1e-4, (prec, v, u, e_pose, e_inv)
+    print("cones (16 pixels): largest pose or inverse-depth error FP64 %.1e FP32 %.1e" % (worst[64], worst[32]))
+
+
+def test_fp32_error_on_the_benchmark_frames_is_reported():
+    """The benchmark's noisy 640x480 frames (20 sweeps per frame): FP32 against the
+    FP64 library per frame, pose and inverse depth (median, p99, max). Reported,
+    not held to the tolerance: on these frames the iteration amplifies rounding
+    (module docstring); the bounds only catch a broken path."""
+    seq = synth.realistic(2, 4)
+    frames = [cuda(seq.frame(k)) for k in range(4)]
+    n0 = cuda(seq.normals(0))
+    trks = {prec: make_tracker(seq.cam, prec, seq.sigma_P, kf_interval=10) for prec in (64, 32)}
+    for k in range(4):
+        for prec, trk in trks.items():
+            trk.track(frames[k], n0 if k == 0 else None, n_iters=seq.sweeps)
+        if k == 0:
+            continue
+        dpose = np.abs(trks[32].pose() - trks[64].pose()).max()
+        a, b = trks[32].state().mu[..., 6], trks[64].state().mu[..., 6]
+        dinv = np.abs(np.expm1(-(a - b)))
+        print("\nbenchmark frame %d, FP32 vs FP64: pose %.1e, inverse depth median %.1e p99 %.1e max %.1e"
+              % (k, dpose, np.median(dinv), np.quantile(dinv, 0.99), dinv.max()))
+        assert dpose < 1e-2 and np.median(dinv) < 0.1
+    assert trks[32].status() == 0 and trks[64].status() == 0
