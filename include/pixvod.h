@@ -244,15 +244,36 @@ pixvod_status pixvod_launch_count(pixvod_handle* h, int64_t* out);
  * L(xi_est, inverse depth) of that frame's result through its n_iters sweeps
  * (Eqs. 2-6 with relinearisation, damping, the belief solve, the mean update
  * and the tangent projection of Sec. 3.4), recomputing each segment of sweeps
- * from its checkpoint with the sweep kernel. Gradients are truncated at the
- * frame start: the state carried from earlier frames is a constant. The
- * derivative is taken in FP64 whatever the handle's precision.
+ * from its checkpoint with the sweep kernel, which then also records each
+ * pixel's discrete decisions (warp validity, Huber branch, skipped update) so
+ * that the derivative follows the branches the forward took. Gradients are
+ * truncated at the frame start: the state carried from earlier frames is a
+ * constant.
+ * Two reverse passes exist (pixvod_set_backward_method):
+ *   PIXVOD_ADJOINT_HANDWRITTEN (default): the hand-written reverse pass, in the
+ *     handle's precision (FP32 or FP64), one thread per pixel, no tape;
+ *   PIXVOD_ADJOINT_TAPE: a reverse-mode tape of the same update in FP64 (about
+ *     230 KB of tape per pixel and sweep, a 10 GB workspace at 320x240), kept to
+ *     cross-check the hand-written pass.
  * ------------------------------------------------------------------------- */
+#define PIXVOD_ADJOINT_HANDWRITTEN 0
+#define PIXVOD_ADJOINT_TAPE 1
 
 /* Device bytes of the recording workspace for frames of at most max_iters
- * sweeps (>= 1) with a checkpoint every checkpoint_every (>= 1) sweeps. */
+ * sweeps (>= 1) with a checkpoint every checkpoint_every (>= 1) sweeps, for the
+ * hand-written reverse pass (no CUDA calls). */
 pixvod_status pixvod_backward_workspace_bytes(const pixvod_intrinsics* K, const pixvod_params* p,
                                               int32_t max_iters, int32_t checkpoint_every, size_t* out_bytes);
+
+/* The same for the tape reverse pass (its tapes are sized by the device's SM
+ * count, which this queries). */
+pixvod_status pixvod_backward_tape_workspace_bytes(const pixvod_intrinsics* K, const pixvod_params* p,
+                                                   int32_t max_iters, int32_t checkpoint_every, size_t* out_bytes);
+
+/* Choose the reverse pass (PIXVOD_ADJOINT_*). Call before pixvod_set_recording,
+ * whose workspace must then be sized by the matching query; ESTATE while
+ * recording is on, EINVAL for an unknown method. */
+pixvod_status pixvod_set_backward_method(pixvod_handle* h, int32_t method);
 
 /* Turns recording on (d_workspace: 256-byte aligned caller device memory of at
  * least pixvod_backward_workspace_bytes, owned by the caller and valid while
@@ -267,11 +288,22 @@ pixvod_status pixvod_set_recording(pixvod_handle* h, void* d_workspace, size_t w
  * Outputs (device, FP64, overwritten): d_grad_sigmas = dL/d(sigma_D, sigma_N)
  * (2), d_grad_Is = dL/d(keyframe intensities) and d_grad_It = dL/d(target
  * frame intensities) (width*height row-major each). check (host, optional,
- * 2 doubles): the largest relative difference between the derivative's own
- * recomputation of a pixel update and the sweep kernel's, and the longest
- * tape. Synchronises the stream. ESTATE if recording is off or the last call
- * was not a non-anchoring target frame tracked with recording on; ENUMERIC if
- * a pixel's derivative tape overflowed. */
+ * 2 doubles): the largest difference between the reverse pass's own
+ * recomputation of a pixel update and the sweep kernel's result, relative to
+ * the magnitude of the output (at least 1; for the hand-written pass, the
+ * projected messages eta - Lambda tau are measured against |eta| + |Lambda tau|,
+ * whose rounding they carry), and (tape pass) the longest tape. Synchronises
+ * the stream.
+ * ESTATE if recording is off or the last call was not a non-anchoring target
+ * frame tracked with recording on; ENUMERIC if a pixel's tape overflowed, or if
+ * that recomputation differs by more than PIXVOD_RECOMPUTE_TOL_FP32 (FP32
+ * arithmetic) or PIXVOD_RECOMPUTE_TOL_FP64 (FP64): the gradients then belong to
+ * a different update than the one the forward ran. In FP64 the recomputation
+ * is exact to rounding; in FP32 two evaluations of the same update differ by
+ * rounding that the belief solve's conditioning amplifies (measured up to
+ * about 1e-2 at 320x240), so the FP32 bound only catches gross differences. */
+#define PIXVOD_RECOMPUTE_TOL_FP32 1e-1
+#define PIXVOD_RECOMPUTE_TOL_FP64 1e-9
 pixvod_status pixvod_backward(pixvod_handle* h, const double* d_grad_xi, const double* d_grad_invdepth,
                               double* d_grad_sigmas, double* d_grad_Is, double* d_grad_It, double* check);
 

@@ -8,7 +8,7 @@ without the library.
 """
 import importlib
 
-_NATIVE = {"ECUDA", "EINVAL", "ENOMEM", "ENUMERIC", "ESTATE", "ETIMEOUT", "FLAG_NONFINITE",
+_NATIVE = {"ADJOINT_HANDWRITTEN", "ADJOINT_TAPE", "ECUDA", "EINVAL", "ENOMEM", "ENUMERIC", "ESTATE", "ETIMEOUT", "FLAG_NONFINITE",
            "SCHED_PLAIN", "SCHED_BATCHED", "SCHED_PERSISTENT", "SCHED_NAMES",
            "TOPOLOGY_GRID", "TOPOLOGY_QUADTREE", "pixvod_intrinsics",
            "FLAG_NONPOS_PIVOT", "FLAG_TIMEOUT", "LIB_PATH", "OK", "PixvodError", "StateView",

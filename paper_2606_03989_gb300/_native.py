@@ -20,6 +20,7 @@ OK, EINVAL, ECUDA, ENUMERIC, ESTATE, ETIMEOUT, ENOMEM = range(7)
 TOPOLOGY_GRID, TOPOLOGY_QUADTREE = 0, 1
 SCHED_PLAIN, SCHED_BATCHED, SCHED_PERSISTENT = 0, 1, 2
 SCHED_NAMES = {SCHED_PLAIN: "plain", SCHED_BATCHED: "batched", SCHED_PERSISTENT: "persistent"}
+ADJOINT_HANDWRITTEN, ADJOINT_TAPE = 0, 1
 FLAG_NONPOS_PIVOT, FLAG_NONFINITE, FLAG_TIMEOUT = 0x1, 0x2, 0x4
 N_PLANES = 151
 N_INPUT_PLANES = 6
@@ -87,6 +88,9 @@ def _load():
         "pixvod_set_recording": (S, [H, P, ctypes.c_size_t, I32, I32]),
         "pixvod_backward": (S, [H, P, P, P, P, P, P]),
         "pixvod_set_backward_window": (S, [H, I32]),
+        "pixvod_set_backward_method": (S, [H, I32]),
+        "pixvod_backward_tape_workspace_bytes": (S, [ctypes.POINTER(pixvod_intrinsics), ctypes.POINTER(pixvod_params),
+                                                     I32, I32, ctypes.POINTER(ctypes.c_size_t)]),
         "pixvod_pose_mean_static": (S, [P, I32, I32, I64, I64, P, P]),
         "pixvod_batch_workspace_bytes": (S, [I32, P, ctypes.POINTER(pixvod_params), ctypes.POINTER(ctypes.c_size_t)]),
         "pixvod_batch_create": (S, [I32, P, ctypes.POINTER(pixvod_params), P, ctypes.c_size_t, P,

@@ -126,32 +126,36 @@ Layout make_layout(const pixvod_intrinsics* K, const pixvod_params* p) {
 }
 
 // Recording for the adjoint (pixvod_set_recording): checkpoints of the state
-// every `every` sweeps, the states of one segment recomputed from a checkpoint,
-// two adjoint states (FP64), descriptors of the recompute launches, the
-// reverse-mode tapes of the adjoint kernel and a few accumulators.
+// every `every` sweeps, the states of one segment recomputed from a checkpoint
+// with each sweep's recorded decisions (a byte per pixel), two adjoint states,
+// descriptors of the recompute launches, a few accumulators and, for the tape
+// cross-check only, the reverse-mode tapes of the tape kernel.
 constexpr int kTapeCap = 8192;            // tape nodes per thread (at most 7133 seen)
 constexpr int kAdjSlotsPerSM = 256;       // adjoint threads per SM (eight blocks of one warp)
 struct RecLayout {
     int n_ckpt, every, max_iters, slots;
-    size_t state_bytes, adj_bytes;
-    size_t off_ckpt, off_seg, off_adj[2], off_desc, off_misc, off_par, off_w, off_tadj, total;
+    size_t state_bytes, adj_bytes, br_bytes;
+    size_t off_ckpt, off_seg, off_br, off_adj[2], off_desc, off_misc, off_par, off_w, off_tadj, total;
 };
 
-RecLayout make_rec_layout(const Layout& L, int max_iters, int every, int n_px, int num_sms) {
+RecLayout make_rec_layout(const Layout& L, int max_iters, int every, int n_px, int num_sms, bool tape) {
     RecLayout R;
     R.every = every;
     R.max_iters = max_iters;
     R.n_ckpt = (max_iters - 1) / every + 1;
-    R.slots = num_sms * kAdjSlotsPerSM;
+    R.slots = tape ? num_sms * kAdjSlotsPerSM : 0;
     const int need = (n_px + pv::ad::ADJ_THREADS - 1) / pv::ad::ADJ_THREADS * pv::ad::ADJ_THREADS;
     if (need < R.slots) R.slots = need;
     R.state_bytes = L.state_bytes;
     R.adj_bytes = align_up((size_t)L.tiles_x * L.tiles_y * pv::TILE_WORDS * sizeof(double), kAlign);
+    R.br_bytes = align_up((size_t)L.tiles_x * L.tiles_y * pv::TILE_PX, kAlign);
     size_t off = 0;
     R.off_ckpt = off;
     off += (size_t)R.n_ckpt * R.state_bytes;
     R.off_seg = off;
     off += (size_t)every * R.state_bytes;
+    R.off_br = off;
+    off += (size_t)every * R.br_bytes;
     for (int b = 0; b < 2; ++b) {
         R.off_adj[b] = off;
         off += R.adj_bytes;
@@ -185,6 +189,8 @@ struct pixvod_handle {
     int64_t launches;
     // recording for the adjoint
     char* rec_ws;
+    size_t rec_bytes;
+    int adj_method;      // PIXVOD_ADJOINT_HANDWRITTEN or PIXVOD_ADJOINT_TAPE
     RecLayout RL;
     int rec_n;           // sweeps of the recorded frame (0: none)
     int rec_window;      // differentiate only the last rec_window sweeps (0: all)
@@ -245,7 +251,7 @@ Scalars* scalars(pixvod_handle* h) { return reinterpret_cast<Scalars*>(h->ws + h
 
 template <typename T>
 pv::SeqDesc<T> seq_desc(pixvod_handle* h, const float* frame, const float* normals) {
-    pv::SeqDesc<T> d;
+    pv::SeqDesc<T> d{};  // every pointer not set below (the recorded-decision buffer) is null
     d.g = geometry<T>(h);
     d.f = factors<T>(h);
     d.state[0] = state_ptr<T>(h, 0);
@@ -255,6 +261,7 @@ pv::SeqDesc<T> seq_desc(pixvod_handle* h, const float* frame, const float* norma
     d.partials = reinterpret_cast<double*>(h->ws + h->L.off_partials);
     d.frame = frame;
     d.normals = normals;
+    d.br = nullptr;
     d.n_tiles = h->L.tiles_x * h->L.tiles_y;
     return d;
 }
@@ -484,10 +491,14 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
     if (s == PIXVOD_OK) s = cuda_status(cudaMemsetAsync(misc, 0, kAlign, st));
     if (s == PIXVOD_OK) s = cuda_status(cudaMemsetAsync(rw + R.off_adj[0], 0, R.adj_bytes, st));
     if (s != PIXVOD_OK) return s;
-    double* adj[2] = {reinterpret_cast<double*>(rw + R.off_adj[0]), reinterpret_cast<double*>(rw + R.off_adj[1])};
+    void* adj[2] = {rw + R.off_adj[0], rw + R.off_adj[1]};
     auto ckpt = [&](int seg) { return reinterpret_cast<T*>(rw + R.off_ckpt + (size_t)seg * R.state_bytes); };
     auto segbuf = [&](int j) { return reinterpret_cast<T*>(rw + R.off_seg + (size_t)(j - 1) * R.state_bytes); };
+    auto brbuf = [&](int j) { return reinterpret_cast<unsigned char*>(rw + R.off_br + (size_t)(j - 1) * R.br_bytes); };
+    const bool tape = h->adj_method == PIXVOD_ADJOINT_TAPE;
+    const bool adj64 = tape || h->p.precision == 64;
     // descriptors of the recompute sweeps: sweep c + j maps S_{c+j-1} to S_{c+j}
+    // and records its decisions in brbuf(j)
     std::vector<pv::SeqDesc<T>> descs(n > 0 ? n : 1);
     const int n_seg = (n + k - 1) / k;
     for (int seg = 0; seg < n_seg; ++seg)
@@ -495,6 +506,7 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
             pv::SeqDesc<T> d = seq_desc<T>(h, nullptr, nullptr);
             d.state[0] = j == 1 ? ckpt(seg) : segbuf(j - 1);
             d.state[1] = segbuf(j);
+            d.br = brbuf(j);
             descs[seg * k + j - 1] = d;
         }
     if (n > 0)
@@ -502,7 +514,7 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
                                         cudaMemcpyHostToDevice, st));
     if (s != PIXVOD_OK) return s;
     const pv::SeqDesc<T>* ddesc = reinterpret_cast<const pv::SeqDesc<T>*>(rw + R.off_desc);
-    pv::AdjArgs A;
+    pv::AdjArgs A{};
     A.g = geometry<double>(h);
     A.state64 = h->p.precision == 64;
     const Factors<double> F = factors<double>(h);
@@ -516,7 +528,7 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
     A.t_huber = F.t_huber;
     A.state_out = state_ptr<T>(h, h->cur);
     h->launches++;
-    if ((s = cuda_status(pv::launch_adjoint_seed(A, g_xi, g_inv, adj[0], st))) != PIXVOD_OK) return s;
+    if ((s = cuda_status(pv::launch_adjoint_seed(A, g_xi, g_inv, adj[0], adj64 ? 1 : 0, st))) != PIXVOD_OK) return s;
     A.I_s = input_ptr<T>(h, 0);
     A.I_t = input_ptr<T>(h, 1);
     A.g_x = input_ptr<T>(h, 2);
@@ -556,10 +568,12 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
             A.state_out = segbuf(j);
             A.adj_out = adj[a];
             A.adj_in = adj[a ^ 1];
+            A.br = brbuf(j);
             if ((s = cuda_status(cudaMemsetAsync(adj[a ^ 1], 0, R.adj_bytes, st))) != PIXVOD_OK) return s;
             h->launches++;
-            if ((s = cuda_status(pv::launch_adjoint_sweep(A, R.slots / pv::ad::ADJ_THREADS, st))) != PIXVOD_OK)
-                return s;
+            s = tape ? cuda_status(pv::launch_adjoint_sweep(A, R.slots / pv::ad::ADJ_THREADS, st))
+                     : cuda_status(pv::launch_adjoint_hw(A, n_tiles, st));
+            if (s != PIXVOD_OK) return s;
             a ^= 1;
         }
     }
@@ -572,13 +586,14 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
     if (s == PIXVOD_OK) s = cuda_status(cudaMemcpyAsync(flags, fl, sizeof(flags), cudaMemcpyDeviceToHost, st));
     if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(st));
     if (s != PIXVOD_OK) return s;
+    double m;
+    memcpy(&m, &mm, sizeof(m));
     if (check) {
-        double m;
-        memcpy(&m, &mm, sizeof(m));
         check[0] = m;
         check[1] = double(flags[1]);
     }
-    return (flags[0] & pv::FLAG_TAPE_FULL) ? PIXVOD_ENUMERIC : PIXVOD_OK;
+    if (flags[0] & pv::FLAG_TAPE_FULL) return PIXVOD_ENUMERIC;
+    return m > (adj64 ? PIXVOD_RECOMPUTE_TOL_FP64 : PIXVOD_RECOMPUTE_TOL_FP32) ? PIXVOD_ENUMERIC : PIXVOD_OK;
 }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
@@ -700,6 +715,8 @@ pixvod_status pixvod_create(const pixvod_intrinsics* K, const pixvod_params* p, 
     h->prof_ms = 0;
     h->prof_launch_base = 0;
     h->rec_ws = nullptr;
+    h->rec_bytes = 0;
+    h->adj_method = PIXVOD_ADJOINT_HANDWRITTEN;
     h->rec_n = 0;
     h->rec_window = 0;
     h->rec_valid = false;
@@ -949,15 +966,28 @@ static pixvod_status device_sms(int* sms) {
     return s;
 }
 
-pixvod_status pixvod_backward_workspace_bytes(const pixvod_intrinsics* K, const pixvod_params* p, int32_t max_iters,
-                                              int32_t checkpoint_every, size_t* out_bytes) {
+static pixvod_status backward_bytes(const pixvod_intrinsics* K, const pixvod_params* p, int32_t max_iters,
+                                    int32_t checkpoint_every, bool tape, size_t* out_bytes) {
     if (!intrinsics_ok(K) || !params_ok(p) || !out_bytes || max_iters < 1 || checkpoint_every < 1)
         return PIXVOD_EINVAL;
     int sms = 0;
-    pixvod_status s = device_sms(&sms);
-    if (s != PIXVOD_OK) return s;
-    *out_bytes = make_rec_layout(make_layout(K, p), max_iters, checkpoint_every, K->width * K->height, sms).total;
+    if (tape) {
+        pixvod_status s = device_sms(&sms);
+        if (s != PIXVOD_OK) return s;
+    }
+    *out_bytes =
+        make_rec_layout(make_layout(K, p), max_iters, checkpoint_every, K->width * K->height, sms, tape).total;
     return PIXVOD_OK;
+}
+
+pixvod_status pixvod_backward_workspace_bytes(const pixvod_intrinsics* K, const pixvod_params* p, int32_t max_iters,
+                                              int32_t checkpoint_every, size_t* out_bytes) {
+    return backward_bytes(K, p, max_iters, checkpoint_every, false, out_bytes);
+}
+
+pixvod_status pixvod_backward_tape_workspace_bytes(const pixvod_intrinsics* K, const pixvod_params* p,
+                                                   int32_t max_iters, int32_t checkpoint_every, size_t* out_bytes) {
+    return backward_bytes(K, p, max_iters, checkpoint_every, true, out_bytes);
 }
 
 pixvod_status pixvod_set_recording(pixvod_handle* h, void* d_workspace, size_t ws_bytes, int32_t max_iters,
@@ -971,13 +1001,24 @@ pixvod_status pixvod_set_recording(pixvod_handle* h, void* d_workspace, size_t w
         return PIXVOD_OK;
     }
     if (!aligned(d_workspace, kAlign) || max_iters < 1 || checkpoint_every < 1) return PIXVOD_EINVAL;
+    const bool tape = h->adj_method == PIXVOD_ADJOINT_TAPE;
     int sms = 0;
-    pixvod_status s = device_sms(&sms);
-    if (s != PIXVOD_OK) return s;
-    RecLayout R = make_rec_layout(h->L, max_iters, checkpoint_every, h->K.width * h->K.height, sms);
+    if (tape) {
+        pixvod_status s = device_sms(&sms);
+        if (s != PIXVOD_OK) return s;
+    }
+    RecLayout R = make_rec_layout(h->L, max_iters, checkpoint_every, h->K.width * h->K.height, sms, tape);
     if (ws_bytes < R.total) return PIXVOD_ENOMEM;
     h->RL = R;
     h->rec_ws = static_cast<char*>(d_workspace);
+    h->rec_bytes = ws_bytes;
+    return PIXVOD_OK;
+}
+
+pixvod_status pixvod_set_backward_method(pixvod_handle* h, int32_t method) {
+    if (!h || (method != PIXVOD_ADJOINT_HANDWRITTEN && method != PIXVOD_ADJOINT_TAPE)) return PIXVOD_EINVAL;
+    if (h->rec_ws) return PIXVOD_ESTATE;  // choose the method before pixvod_set_recording
+    h->adj_method = method;
     return PIXVOD_OK;
 }
 
@@ -1280,6 +1321,8 @@ pixvod_status pixvod_batch_create(int32_t n, const pixvod_intrinsics* K, const p
         h.prof_ms = 0;
         h.prof_launch_base = 0;
         h.rec_ws = nullptr;
+        h.rec_bytes = 0;
+        h.adj_method = PIXVOD_ADJOINT_HANDWRITTEN;
         h.rec_n = 0;
         h.rec_window = 0;
         h.rec_valid = false;

@@ -1,18 +1,211 @@
-// Adjoint kernels of the sweep (reverse-mode per pixel, see pv_adjoint.cuh),
-// compiled on their own: their launchers are called from pixvod.cu.
+// Adjoint kernels of the sweep, compiled on their own: their launchers are
+// called from pixvod.cu. Two reverse passes of one sweep exist:
+//  - k_adjoint_hw<T>: the hand-written reverse pass (pv_adjoint_hw.cuh) in the
+//    state's precision, one thread per pixel, no tape; the product path;
+//  - k_adjoint_sweep: a reverse-mode tape of the same update in FP64
+//    (pv_adjoint.cuh), kept to cross-check the hand-written pass.
 #include "pv_adjoint.cuh"
+#include "pv_adjoint_hw.cuh"
 
 namespace pv {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T ld(const void* p, size_t i) {
+    return static_cast<const T*>(p)[i];
+}
+
+// I/O of one pixel's reverse pass in the kernel: reads from the state before
+// the sweep and the adjoint of the state after it; adds the input adjoints to
+// the adjoint of the previous state (atomically: neighbours add to the same
+// planes), to dI_t (atomically) and to thread-local sums.
+template <typename T>
+struct KernelIO {
+    const T* Sin;    // S_{s-1}
+    const T* Sout;   // S_s
+    const T* Ao;     // adjoint of S_s
+    T* Ai;           // adjoint of S_{s-1}
+    double* dI_t;
+    int W, H;
+    size_t si, sj[4];
+    int tx[4], ty[4];
+    T Is, tapv[12];
+    double mm, dIs, lamD, isD, lamN;
+
+    __device__ T mu(int q) const { return Sin[si + q * TILE_PX]; }
+    __device__ T msg(int k, int q) const { return Sin[si + (PL_ID + ID_STRIDE * k + q) * TILE_PX]; }
+    __device__ T nm(int q) const { return Sin[si + (PL_NM + q) * TILE_PX]; }
+    __device__ T nb(int k, int q) const { return Sin[sj[k] + nb_plane(q, k) * TILE_PX]; }
+    __device__ T I_s() const { return Is; }
+    __device__ T tap(int q) const { return tapv[q]; }
+    __device__ T ybar(int q) const { return Ao[si + q * TILE_PX]; }
+    __device__ void out(int q, T y, T scale) {
+        const double ref = double(Sout[si + q * TILE_PX]);
+        const double e = fabs(double(y) - ref) / fmax(double(scale), fabs(ref));
+        mm = e > mm ? e : mm;
+    }
+    __device__ void add_mu(int q, T v) { atomicAdd(Ai + si + q * TILE_PX, v); }
+    __device__ void add_msg(int k, int q, T v) { atomicAdd(Ai + si + (PL_ID + ID_STRIDE * k + q) * TILE_PX, v); }
+    __device__ void add_nm(int q, T v) { atomicAdd(Ai + si + (PL_NM + q) * TILE_PX, v); }
+    __device__ void add_nb(int k, int q, T v) { atomicAdd(Ai + sj[k] + nb_plane(q, k) * TILE_PX, v); }
+    __device__ void add_Is(T v) { dIs += double(v); }
+    // taps 0-3 of I_t directly; 4-7 of g_x and 8-11 of g_y through the central
+    // differences of the target ingest (replicated borders)
+    __device__ void add_tap(int q, T v) {
+        const int m = q >> 2, xq = tx[q & 3], yq = ty[q & 3];
+        const size_t row = (size_t)yq * W;
+        if (m == 0) {
+            atomicAdd(dI_t + row + xq, double(v));
+        } else if (m == 1) {
+            scatter_gradient_tap(dI_t, W, (int)(row + (xq > 0 ? xq - 1 : 0)), (int)(row + (xq + 1 < W ? xq + 1 : W - 1)),
+                                 double(v));
+        } else {
+            scatter_gradient_tap(dI_t, W, (yq > 0 ? yq - 1 : 0) * W + xq, (yq + 1 < H ? yq + 1 : H - 1) * W + xq,
+                                 double(v));
+        }
+    }
+    __device__ void add_lamD(T v) { lamD += double(v); }
+    __device__ void add_isD(T v) { isD += double(v); }
+    __device__ void add_lamN(T v) { lamN += double(v); }
+};
+
+// The hand-written adjoint of one sweep: block = one state tile (32 x 4 pixels),
+// thread = one pixel, which runs hw::pixel_vjp on its update: the recomputed
+// update is compared with the sweep kernel's result, and the adjoints of the
+// update's inputs are added to the adjoint state of the previous sweep (its own
+// planes and the planes it read from its neighbours), to dI_s, dI_t (the
+// bilinear taps, and the central differences behind g_x, g_y) and to the factor
+// weights.
+template <typename T>
+__global__ void __launch_bounds__(TILE_PX) k_adjoint_hw(const AdjArgs A) {
+    const Geometry<double>& g = A.g;
+    const int W = g.W, H = g.H;
+    const int tile = blockIdx.x, lane = threadIdx.x;
+    const int u = (tile % g.tiles_x) * TILE_W + lane % TILE_W;
+    const int v = (tile / g.tiles_x) * TILE_H + lane / TILE_W;
+    __shared__ double red[3];
+    if (lane < 3) red[lane] = 0.0;
+    __syncthreads();
+    if (u < W && v < H) {
+        KernelIO<T> io;
+        io.Sin = static_cast<const T*>(A.state_in);
+        io.Sout = static_cast<const T*>(A.state_out);
+        io.Ao = static_cast<const T*>(A.adj_out);
+        io.Ai = static_cast<T*>(A.adj_in);
+        io.dI_t = A.dI_t;
+        io.W = W;
+        io.H = H;
+        io.si = (size_t)tile * TILE_WORDS + lane;
+        io.mm = io.dIs = io.lamD = io.isD = io.lamN = 0.0;
+        const size_t ii = (size_t)v * g.pitch + u;
+        hw::PixCtx<T> c;
+        c.u = T(u);
+        c.v = T(v);
+        c.W = W;
+        c.H = H;
+        c.fx = T(g.fx);
+        c.fy = T(g.fy);
+        c.cx = T(g.cx);
+        c.cy = T(g.cy);
+        c.ifx = T(g.ifx);
+        c.ify = T(g.ify);
+        c.d_prior = T(A.d_prior);
+        c.lam_P = T(A.lam_P);
+        c.lam_Z = T(A.lam_Z);
+        c.lam_R = T(A.lam_R);
+        c.beta = T(A.beta);
+        c.t_huber = T(A.t_huber);
+        c.lam_D = T(A.lam_D);
+        c.inv_sigma_D = T(A.inv_sigma_D);
+        c.lam_N = T(A.lam_N);
+        c.br = A.br[(size_t)tile * TILE_PX + lane];
+        for (int k = 0; k < 4; ++k) {
+            const int nu = u + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+            const int nv = v + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+            c.has[k] = nu >= 0 && nu < W && nv >= 0 && nv < H;
+            io.sj[k] = c.has[k] ? state_index(nu, nv, g.tiles_x) : 0;
+            c.m[k] = T(0);
+            if (c.has[k])
+                c.m[k] = k == 0 ? ld<T>(A.m_x, ii - 1)
+                                : (k == 1 ? ld<T>(A.m_x, ii) : (k == 2 ? ld<T>(A.m_y, ii - g.pitch) : ld<T>(A.m_y, ii)));
+        }
+        io.Is = ld<T>(A.I_s, ii);
+        // the bilinear cell of the warp at the current mean, with the sweep
+        // kernel's arithmetic
+        {
+            T xi[6], R[9], t[3];
+            for (int q = 0; q < 6; ++q) xi[q] = io.mu(q);
+            se3_exp(xi, R, t);
+            const T z = v_exp(io.mu(6));
+            const T Xs[3] = {z * (c.u - c.cx) * c.ifx, z * (c.v - c.cy) * c.ify, z};
+            T Xt[3];
+            mat3_vec(R, Xs, Xt);
+            Xt[0] += t[0];
+            Xt[1] += t[1];
+            Xt[2] += t[2];
+            const bool valid = (c.br & BR_VALID) != 0;
+            const T iz = valid ? v_div(T(1), Xt[2]) : T(0);
+            T x = c.fx * Xt[0] * iz + c.cx;
+            T y = c.fy * Xt[1] * iz + c.cy;
+            c.clamp_x = x < T(0) || x > T(W - 1);
+            c.clamp_y = y < T(0) || y > T(H - 1);
+            x = x < T(0) ? T(0) : (x > T(W - 1) ? T(W - 1) : x);
+            y = y < T(0) ? T(0) : (y > T(H - 1) ? T(H - 1) : y);
+            int x0 = valid ? (int)v_floor(x) : 0, y0 = valid ? (int)v_floor(y) : 0;
+            x0 = min(x0, W - 1);
+            y0 = min(y0, H - 1);
+            const int x1 = min(x0 + 1, W - 1), y1 = min(y0 + 1, H - 1);
+            c.x0 = x0;
+            c.y0 = y0;
+            io.tx[0] = x0;
+            io.ty[0] = y0;
+            io.tx[1] = x1;
+            io.ty[1] = y0;
+            io.tx[2] = x0;
+            io.ty[2] = y1;
+            io.tx[3] = x1;
+            io.ty[3] = y1;
+        }
+        for (int q = 0; q < 4; ++q) {
+            const size_t ti = (size_t)io.ty[q] * g.pitch + io.tx[q];
+            io.tapv[q] = ld<T>(A.I_t, ti);
+            io.tapv[4 + q] = ld<T>(A.g_x, ti);
+            io.tapv[8 + q] = ld<T>(A.g_y, ti);
+        }
+        hw::pixel_vjp(io, c);
+        atomic_max_nonneg(A.mismatch, io.mm);
+        A.dI_s[(size_t)v * W + u] += io.dIs;
+        atomicAdd(&red[0], io.lamD);
+        atomicAdd(&red[1], io.isD);
+        atomicAdd(&red[2], io.lamN);
+    }
+    __syncthreads();
+    if (lane < 3 && red[lane] != 0.0) atomicAdd(A.dparam + lane, red[lane]);
+}
+
+}  // namespace
 
 cudaError_t launch_adjoint_sweep(const AdjArgs& A, int blocks, cudaStream_t st) {
     k_adjoint_sweep<<<blocks, ad::ADJ_THREADS, 0, st>>>(A);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_seed(const AdjArgs& A, const double* grad_xi, const double* grad_invdepth, double* adj,
-                                cudaStream_t st) {
+cudaError_t launch_adjoint_hw(const AdjArgs& A, int n_tiles, cudaStream_t st) {
+    if (A.state64)
+        k_adjoint_hw<double><<<n_tiles, TILE_PX, 0, st>>>(A);
+    else
+        k_adjoint_hw<float><<<n_tiles, TILE_PX, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_seed(const AdjArgs& A, const double* grad_xi, const double* grad_invdepth, void* adj,
+                                int adj64, cudaStream_t st) {
     dim3 block(32, 4), grid((A.g.W + 31) / 32, (A.g.H + 3) / 4);
-    k_adjoint_seed<<<grid, block, 0, st>>>(A, grad_xi, grad_invdepth, adj);
+    if (adj64)
+        k_adjoint_seed<double><<<grid, block, 0, st>>>(A, grad_xi, grad_invdepth, static_cast<double*>(adj));
+    else
+        k_adjoint_seed<float><<<grid, block, 0, st>>>(A, grad_xi, grad_invdepth, static_cast<float*>(adj));
     return cudaGetLastError();
 }
 

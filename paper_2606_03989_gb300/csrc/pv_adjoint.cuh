@@ -173,7 +173,9 @@ struct PixelCtx {
     bool has[4];           // the neighbour of direction k is in the image
     double m[4];           // normal edge measurement of direction k
     double d_prior, lam_P, lam_Z, lam_R, beta, t_huber;
-    bool warp_valid;       // the warp decided by the caller (same arithmetic)
+    bool warp_valid;       // the photometric factor was active in the sweep (recorded)
+    bool huber;            // its Huber weight was below 1 (recorded)
+    bool skip;             // the sweep set this pixel's tau to 0 (recorded)
     int x0, y0;            // bilinear cell of the warped point
 };
 
@@ -326,7 +328,6 @@ __device__ void pixel_update(const PixelIn<S>& in, const PixelCtx& c, S* y) {
             gx = bilin4(in.tap + 4, ax, ay);
             gy = bilin4(in.tap + 8, ax, ay);
             r = in.I_s - It;
-            valid = v_finite(r) && v_finite(gx) && v_finite(gy);
         }
         if (valid) {
             const S a0 = -gx * S(c.fx) * iz, a1 = -gy * S(c.fy) * iz;
@@ -343,7 +344,7 @@ __device__ void pixel_update(const PixelIn<S>& in, const PixelCtx& c, S* y) {
             J[6] = b[0] * Xs[0] + b[1] * Xs[1] + b[2] * Xs[2];
             const S M = v_abs(r) * in.inv_sigma_D;
             const S th = S(c.t_huber);
-            const S w = M > th ? (S(2) * th * M - th * th) / (M * M) : S(1);
+            const S w = c.huber ? (S(2) * th * M - th * th) / (M * M) : S(1);
             alpha = w * in.lam_D;
             rph = r;
         }
@@ -376,9 +377,8 @@ __device__ void pixel_update(const PixelIn<S>& in, const PixelCtx& c, S* y) {
         for (int q = 0; q < 6; ++q) tau[q] = gp[q] - coef * up[q];
         tau[6] = hd - coef * zd;
     }
-    bool fin = true;
-    for (int q = 0; q < 7; ++q) fin = fin && v_finite(tau[q]);
-    if (!ok || !fin)
+    (void)ok;
+    if (c.skip)
         for (int q = 0; q < 7; ++q) tau[q] = S(0);
     // mean update and outputs
     {
@@ -490,7 +490,11 @@ __global__ void __launch_bounds__(ad::ADJ_THREADS) k_adjoint_sweep(const AdjArgs
             double xi[6], R[9], t[3], x, y;
             for (int q = 0; q < 6; ++q) xi[q] = in.mu[q].v;
             se3_exp(xi, R, t);
-            c.warp_valid = warp_point(c, R, t, in.mu[6].v, &x, &y);
+            warp_point(c, R, t, in.mu[6].v, &x, &y);
+            const unsigned char br = A.br[(size_t)(si / TILE_WORDS) * TILE_PX + si % TILE_PX];
+            c.warp_valid = (br & BR_VALID) != 0;
+            c.huber = (br & BR_HUBER) != 0;
+            c.skip = (br & BR_SKIP) != 0;
             x = x < 0.0 ? 0.0 : (x > double(W - 1) ? double(W - 1) : x);
             y = y < 0.0 ? 0.0 : (y > double(H - 1) ? double(H - 1) : y);
             int x0 = c.warp_valid ? (int)floor(x) : 0, y0 = c.warp_valid ? (int)floor(y) : 0;
@@ -532,7 +536,7 @@ __global__ void __launch_bounds__(ad::ADJ_THREADS) k_adjoint_sweep(const AdjArgs
         atomicMax(A.max_nodes, (unsigned)n);
         double* adj = ad::tape_ctl.adj;
         for (int k = 0; k < n; ++k) adj[ad::tape_at(k)] = 0.0;
-        const double* Ao = A.adj_out + si;
+        const double* Ao = static_cast<const double*>(A.adj_out) + si;
         for (int q = 0; q < N_PLANES; ++q)
             if (y[q].i >= 0) adj[ad::tape_at(y[q].i)] += Ao[q * TILE_PX];
         for (int k = n - 1; k >= 0; --k) {
@@ -547,13 +551,13 @@ __global__ void __launch_bounds__(ad::ADJ_THREADS) k_adjoint_sweep(const AdjArgs
         auto gl = [&](const Rev& r) { return r.i >= 0 ? adj[ad::tape_at(r.i)] : 0.0; };
 
         // scatter the adjoints of the inputs
-        double* Ai = A.adj_in + si;
+        double* Ai = static_cast<double*>(A.adj_in) + si;
         for (int q = 0; q < 7; ++q) atomicAdd(Ai + q * TILE_PX, gl(in.mu[q]));
         for (int q = 0; q < MSG_PLANES; ++q) atomicAdd(Ai + (PL_ID + q) * TILE_PX, gl(in.msg[q]));
         for (int q = 0; q < 8; ++q) atomicAdd(Ai + (PL_NM + q) * TILE_PX, gl(in.nm[q]));
         for (int k = 0; k < 4; ++k) {
             if (!c.has[k]) continue;
-            double* Aj = A.adj_in + state_index(nu[k], nv[k], g.tiles_x);
+            double* Aj = static_cast<double*>(A.adj_in) + state_index(nu[k], nv[k], g.tiles_x);
             for (int q = 0; q < NB_VALS; ++q) atomicAdd(Aj + nb_plane(q, k) * TILE_PX, gl(in.nb[k][q]));
         }
         A.dI_s[(size_t)v * W + u] += gl(in.I_s);
@@ -585,17 +589,18 @@ __global__ void k_sigma_grads(const double* __restrict__ dparam, double sD, doub
 // adjoint of the frame's loss inputs: xi_est = mean_i mu_i[0:6] and the inverse
 // depth exp(-mu_i[6]), from dL/dxi_est (6) and dL/d(inverse depth) (W x H), at
 // the state A.state_out
+template <typename TA>
 __global__ void k_adjoint_seed(const AdjArgs A, const double* __restrict__ grad_xi,
-                               const double* __restrict__ grad_invdepth, double* __restrict__ adj) {
+                               const double* __restrict__ grad_invdepth, TA* __restrict__ adj) {
     const Geometry<double>& g = A.g;
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y * blockDim.y + threadIdx.y;
     if (u >= g.W || v >= g.H) return;
     const size_t si = state_index(u, v, g.tiles_x);
     const double n = double(g.W) * double(g.H);
-    for (int q = 0; q < 6; ++q) adj[si + q * TILE_PX] = grad_xi ? grad_xi[q] / n : 0.0;
+    for (int q = 0; q < 6; ++q) adj[si + q * TILE_PX] = TA(grad_xi ? grad_xi[q] / n : 0.0);
     const double gi = grad_invdepth ? grad_invdepth[(size_t)v * g.W + u] : 0.0;
-    adj[si + 6 * TILE_PX] = -gi * exp(-ldT(A.state_out, si + 6 * TILE_PX, A.state64));
+    adj[si + 6 * TILE_PX] = TA(-gi * exp(-ldT(A.state_out, si + 6 * TILE_PX, A.state64)));
 }
 
 }  // namespace pv

@@ -24,15 +24,18 @@ struct TapeCtl {
 constexpr unsigned FLAG_TAPE_FULL = 0x8u;  // a pixel's tape overflowed: its gradient is missing
 
 // Arguments of the adjoint of one sweep. State buffers and input planes hold
-// FP64 when state64 is set, FP32 otherwise; adjoints and gradients are FP64.
+// FP64 when state64 is set, FP32 otherwise. The adjoint states are FP64 for the
+// tape kernel and in the state's precision for the hand-written one; the
+// gradients of the inputs and factor weights are FP64.
 struct AdjArgs {
     Geometry<double> g;
     int state64;
     double lam_D, inv_sigma_D, lam_N, lam_P, lam_Z, lam_R, beta, t_huber, d_prior;
     const void* state_in;          // S_{s-1} (tile-major)
     const void* state_out;         // S_s, for the check of the recomputed update
-    const double* adj_out;         // adjoint of S_s (tile-major, 151 planes)
-    double* adj_in;                // adjoint of S_{s-1}, accumulated
+    const void* adj_out;           // adjoint of S_s (tile-major, 151 planes)
+    void* adj_in;                  // adjoint of S_{s-1}, accumulated
+    const unsigned char* br;       // the sweep's recorded decisions (BR_*, tile-major pixel index)
     const void* I_s;               // input planes (row-major, pitched)
     const void* I_t;
     const void* g_x;
@@ -48,12 +51,17 @@ struct AdjArgs {
     ad::TapeCtl tape;
 };
 
-// adjoint of one sweep, `blocks` blocks of ADJ_THREADS threads striding over the pixels
+// adjoint of one sweep by the reverse-mode tape (FP64), `blocks` blocks of
+// ADJ_THREADS threads striding over the pixels
 cudaError_t launch_adjoint_sweep(const AdjArgs& A, int blocks, cudaStream_t st);
+// adjoint of one sweep by the hand-written reverse pass, in the state's
+// precision: one block of 128 threads per state tile
+cudaError_t launch_adjoint_hw(const AdjArgs& A, int n_tiles, cudaStream_t st);
 // adjoint of xi_est = mean mu[0:6] and of the inverse depth exp(-mu[6]) at the
-// state A.state_out, written into adj (all other planes left as they are)
-cudaError_t launch_adjoint_seed(const AdjArgs& A, const double* grad_xi, const double* grad_invdepth, double* adj,
-                                cudaStream_t st);
+// state A.state_out, written into adj (all other planes left as they are), FP64
+// (adj64) or FP32
+cudaError_t launch_adjoint_seed(const AdjArgs& A, const double* grad_xi, const double* grad_invdepth, void* adj,
+                                int adj64, cudaStream_t st);
 // dL/d(sigma_D, sigma_N) from the adjoints of lam_D, 1/sigma_D and lam_N
 cudaError_t launch_sigma_grads(const double* dparam, double sigma_D, double sigma_N, double* out, cudaStream_t st);
 

@@ -22,6 +22,7 @@ struct SeqDesc {
     double* partials;
     const float* frame;    // registered input buffers
     const float* normals;
+    unsigned char* br;     // decisions of the sweep, recorded for the adjoint (or null)
     int n_tiles;
 };
 
@@ -44,6 +45,7 @@ __device__ __forceinline__ SweepArgs<T> seq_args(const SeqDesc<T>& d, int cur) {
     a.m_x = d.in_planes[4];
     a.m_y = d.in_planes[5];
     a.sc = d.sc;
+    a.br = d.br;
     return a;
 }
 

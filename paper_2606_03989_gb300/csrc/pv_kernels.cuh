@@ -26,6 +26,7 @@
 // exceed its other pose information by more than float32 resolves.
 #pragma once
 
+#include "pv_branch.h"
 #include "pv_math.cuh"
 
 namespace pv {
@@ -93,7 +94,11 @@ struct SweepArgs {
     const T* __restrict__ m_x;
     const T* __restrict__ m_y;
     Scalars* sc;
+    // when set, each pixel's discrete decisions of this sweep (BR_* bits) are
+    // written here (tile-major pixel index), for the adjoint
+    unsigned char* br;
 };
+
 
 // ---------------------------------------------------------------------------
 // a0: frame ingest
@@ -440,6 +445,7 @@ __device__ __forceinline__ bool sweep_pixel(const SweepArgs<T>& a, int tx, int t
     T J[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) J[q] = T(0);
+    unsigned char br = 0;
 
     // --- a1: photometric factor (Eqs. 2, 3) at the current mean (it enters only
     // the belief below, so it is evaluated after the pairwise messages) ---
@@ -489,9 +495,11 @@ __device__ __forceinline__ bool sweep_pixel(const SweepArgs<T>& a, int tx, int t
             J[5] = b[2];
             J[6] = b[0] * Xs[0] + b[1] * Xs[1] + b[2] * Xs[2];
             T M = v_abs(r) * F.inv_sigma_D;
-            T w = M > F.t_huber ? v_div(T(2) * F.t_huber * M - F.t_huber * F.t_huber, M * M) : T(1);
+            const bool hub = M > F.t_huber;
+            T w = hub ? v_div(T(2) * F.t_huber * M - F.t_huber * F.t_huber, M * M) : T(1);
             alpha = w * F.lam_D;
             rph = r;
+            br = hub ? (BR_VALID | BR_HUBER) : BR_VALID;
         }
     }
     // --- a4: belief, mean update, tangent projection ---
@@ -540,9 +548,11 @@ __device__ __forceinline__ bool sweep_pixel(const SweepArgs<T>& a, int tx, int t
     if (!ok) flags |= FLAG_NONPOS_PIVOT;
     if (!ok || !fin) {
         if (!fin) flags |= FLAG_NONFINITE;
+        br |= BR_SKIP;
 #pragma unroll
         for (int q = 0; q < 7; ++q) tau[q] = T(0);
     }
+    if (a.br) a.br[tile * TILE_PX + tid] = br;
     // mu <- mu (+) tau
     {
         T Rt[9], tt[3], Rn[9], tn[3], xn[6];

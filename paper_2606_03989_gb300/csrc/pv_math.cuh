@@ -12,31 +12,44 @@
 #include <math.h>
 #include <stdint.h>
 
+// Every function here is also compiled for the host (PV_HD), so that the same
+// arithmetic can be exercised by host-side checks; on the device the scalar
+// wrappers below select CUDA's device functions.
+#define PV_HD __host__ __device__ __forceinline__
+
 namespace pv {
 
 // ---------------------------------------------------------------------------
 // scalar wrappers (precise CUDA math functions, selected by type)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float v_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double v_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float v_exp(float x) { return expf(x); }
-__device__ __forceinline__ double v_exp(double x) { return exp(x); }
-__device__ __forceinline__ float v_atan2(float y, float x) { return atan2f(y, x); }
-__device__ __forceinline__ double v_atan2(double y, double x) { return atan2(y, x); }
-__device__ __forceinline__ float v_floor(float x) { return floorf(x); }
-__device__ __forceinline__ double v_floor(double x) { return floor(x); }
-__device__ __forceinline__ float v_abs(float x) { return fabsf(x); }
-__device__ __forceinline__ double v_abs(double x) { return fabs(x); }
-__device__ __forceinline__ void v_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
-__device__ __forceinline__ void v_sincos(double x, double* s, double* c) { sincos(x, s, c); }
-__device__ __forceinline__ bool v_finite(float x) { return isfinite(x); }
-__device__ __forceinline__ bool v_finite(double x) { return isfinite(x); }
+PV_HD float v_sqrt(float x) { return sqrtf(x); }
+PV_HD double v_sqrt(double x) { return sqrt(x); }
+PV_HD float v_exp(float x) { return expf(x); }
+PV_HD double v_exp(double x) { return exp(x); }
+PV_HD float v_atan2(float y, float x) { return atan2f(y, x); }
+PV_HD double v_atan2(double y, double x) { return atan2(y, x); }
+PV_HD float v_floor(float x) { return floorf(x); }
+PV_HD double v_floor(double x) { return floor(x); }
+PV_HD float v_abs(float x) { return fabsf(x); }
+PV_HD double v_abs(double x) { return fabs(x); }
+PV_HD bool v_finite(float x) { return isfinite(x); }
+PV_HD bool v_finite(double x) { return isfinite(x); }
 // reciprocal square root and quotient: the float path uses the approximate
 // hardware forms (a few ulp), the double (verification) path the exact ones
-__device__ __forceinline__ float v_rsqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double v_rsqrt(double x) { return rsqrt(x); }
-__device__ __forceinline__ float v_div(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double v_div(double a, double b) { return a / b; }
+#ifdef __CUDA_ARCH__
+PV_HD void v_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+PV_HD void v_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+PV_HD float v_rsqrt(float x) { return rsqrtf(x); }
+PV_HD double v_rsqrt(double x) { return rsqrt(x); }
+PV_HD float v_div(float a, float b) { return __fdividef(a, b); }
+#else
+PV_HD void v_sincos(float x, float* s, float* c) { *s = sinf(x); *c = cosf(x); }
+PV_HD void v_sincos(double x, double* s, double* c) { *s = sin(x); *c = cos(x); }
+PV_HD float v_rsqrt(float x) { return 1.0f / sqrtf(x); }
+PV_HD double v_rsqrt(double x) { return 1.0 / sqrt(x); }
+PV_HD float v_div(float a, float b) { return a / b; }
+#endif
+PV_HD double v_div(double a, double b) { return a / b; }
 
 // Precision-dependent series limits: below ab_series_max the A/B quotients use
 // their power series to t^6; below 1 rad (C) and d_series_max (D) the other
@@ -68,7 +81,7 @@ __host__ __device__ constexpr double series_C_coef(int k) {
 }
 
 template <typename T, int K, int N>
-__device__ __forceinline__ T series_C_from(T t2) {
+PV_HD T series_C_from(T t2) {
     constexpr double c = series_C_coef(K);
     if constexpr (K + 1 < N)
         return T(c) + t2 * series_C_from<T, K + 1, N>(t2);
@@ -77,7 +90,7 @@ __device__ __forceinline__ T series_C_from(T t2) {
 }
 
 template <typename T>
-__device__ __forceinline__ T series_C(T t2) {
+PV_HD T series_C(T t2) {
     return series_C_from<T, 0, Prec<T>::c_terms>(t2);
 }
 
@@ -85,20 +98,20 @@ __device__ __forceinline__ T series_C(T t2) {
 // V^-1; from the Laurent series of cot: 1/12 + t^2/720 + t^4/30240 + t^6/1209600
 // + t^8/47900160 + t^10/1892437580.3 + ... (used below d_series_max).
 template <typename T>
-__device__ __forceinline__ T series_D(T t2) {
+PV_HD T series_D(T t2) {
     return T(1) / T(12) + t2 * (T(1) / T(720) + t2 * (T(1) / T(30240) + t2 * (T(1) / T(1209600) +
            t2 * (T(1) / T(47900160) + t2 * (T(1) / T(1892437580.3183))))));
 }
 
 // sin t / t = 1 - t^2/3! + t^4/5! - t^6/7!; (1 - cos t)/t^2 = 1/2! - t^2/4! + t^4/6! - t^6/8!
 template <typename T>
-__device__ __forceinline__ void series_AB(T t2, T* A, T* B) {
+PV_HD void series_AB(T t2, T* A, T* B) {
     *A = T(1) - t2 * (T(1) / T(6) - t2 * (T(1) / T(120) - t2 * (T(1) / T(5040))));
     *B = T(0.5) - t2 * (T(1) / T(24) - t2 * (T(1) / T(720) - t2 * (T(1) / T(40320))));
 }
 
 template <typename T>
-__device__ __forceinline__ void coef_AB(T t, T* A, T* B) {
+PV_HD void coef_AB(T t, T* A, T* B) {
     if (t < Prec<T>::ab_series_max) {
         series_AB(t * t, A, B);
     } else {
@@ -112,13 +125,13 @@ __device__ __forceinline__ void coef_AB(T t, T* A, T* B) {
 }
 
 template <typename T>
-__device__ __forceinline__ T coef_C(T t, T A) {
+PV_HD T coef_C(T t, T A) {
     if (t < T(1)) return series_C(t * t);
     return (T(1) - A) / (t * t);
 }
 
 template <typename T>
-__device__ __forceinline__ T coef_D(T t, T A, T B) {
+PV_HD T coef_D(T t, T A, T B) {
     if (t < Prec<T>::d_series_max) return series_D(t * t);
     return (T(1) - A / (T(2) * B)) / (t * t);
 }
@@ -127,7 +140,7 @@ __device__ __forceinline__ T coef_D(T t, T A, T B) {
 // 3x3 helpers (row-major)
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void mat3_mul(const T* a, const T* b, T* c) {
+PV_HD void mat3_mul(const T* a, const T* b, T* c) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -136,20 +149,20 @@ __device__ __forceinline__ void mat3_mul(const T* a, const T* b, T* c) {
 }
 
 template <typename T>
-__device__ __forceinline__ void mat3_vec(const T* a, const T* x, T* y) {
+PV_HD void mat3_vec(const T* a, const T* x, T* y) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) y[i] = a[3 * i] * x[0] + a[3 * i + 1] * x[1] + a[3 * i + 2] * x[2];
 }
 
 template <typename T>
-__device__ __forceinline__ void mat3T_vec(const T* a, const T* x, T* y) {
+PV_HD void mat3T_vec(const T* a, const T* x, T* y) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) y[i] = a[i] * x[0] + a[3 + i] * x[1] + a[6 + i] * x[2];
 }
 
 // M = I + a W + b W^2 for W = [w]x, using W^2 = w w^T - |w|^2 I
 template <typename T>
-__device__ __forceinline__ void so3_poly(const T* w, T a, T b, T* M) {
+PV_HD void so3_poly(const T* w, T a, T b, T* M) {
     T t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
     M[0] = T(1) + b * (w[0] * w[0] - t2);
     M[4] = T(1) + b * (w[1] * w[1] - t2);
@@ -166,7 +179,7 @@ __device__ __forceinline__ void so3_poly(const T* w, T a, T b, T* M) {
 // their power series in t^2, so small rotations take no square root, division
 // or trigonometric call.
 template <typename T>
-__device__ __forceinline__ void se3_exp(const T* xi, T* R, T* t) {
+PV_HD void se3_exp(const T* xi, T* R, T* t) {
     T t2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
     T A, B, C;
     if (t2 < Prec<T>::ab_series_max * Prec<T>::ab_series_max) {
@@ -188,14 +201,12 @@ __device__ __forceinline__ void se3_exp(const T* xi, T* R, T* t) {
 // asin_series_max (and c > 0) t / s = asin(s) / s comes from the arcsine series
 // 1 + s^2/6 + 3 s^4/40 + 5 s^6/112 + 35 s^8/1152 and t^2 = s^2 (t / s)^2, so small
 // rotations take no square root, division or trigonometric call.
+// The logarithm from w = vee(R - R^T)/2, c = (tr R - 1)/2 and t (se3_log below
+// computes w and c; the adjoint differentiates this part in w, c and t).
 template <typename T>
-__device__ __forceinline__ void se3_log(const T* R, const T* t, T* xi) {
+PV_HD void se3_log_wct(T w0, T w1, T w2, T c, const T* t, T* xi) {
     static_assert(Prec<T>::asin_series_max <= Prec<T>::d_series_max / 2, "series D range");
-    T w0 = T(0.5) * (R[7] - R[5]);
-    T w1 = T(0.5) * (R[2] - R[6]);
-    T w2 = T(0.5) * (R[3] - R[1]);
     T s2 = w0 * w0 + w1 * w1 + w2 * w2;
-    T c = T(0.5) * (R[0] + R[4] + R[8] - T(1));
     T ratio, D;
     if (s2 < Prec<T>::asin_series_max * Prec<T>::asin_series_max && c > T(0)) {
         ratio = T(1) + s2 * (T(1) / T(6) + s2 * (T(3) / T(40) + s2 * (T(5) / T(112) + s2 * (T(35) / T(1152)))));
@@ -215,9 +226,15 @@ __device__ __forceinline__ void se3_log(const T* R, const T* t, T* xi) {
     mat3_vec(Vi, t, xi + 3);
 }
 
+template <typename T>
+PV_HD void se3_log(const T* R, const T* t, T* xi) {
+    se3_log_wct(T(0.5) * (R[7] - R[5]), T(0.5) * (R[2] - R[6]), T(0.5) * (R[3] - R[1]),
+                T(0.5) * (R[0] + R[4] + R[8] - T(1)), t, xi);
+}
+
 // (R1, t1) * (R2, t2)
 template <typename T>
-__device__ __forceinline__ void se3_mul(const T* R1, const T* t1, const T* R2, const T* t2, T* R, T* t) {
+PV_HD void se3_mul(const T* R1, const T* t1, const T* R2, const T* t2, T* R, T* t) {
     mat3_mul(R1, R2, R);
     mat3_vec(R1, t2, t);
     t[0] += t1[0];
@@ -227,7 +244,7 @@ __device__ __forceinline__ void se3_mul(const T* R1, const T* t1, const T* R2, c
 
 // (R1, t1)^-1 * (R2, t2) = (R1^T R2, R1^T (t2 - t1))
 template <typename T>
-__device__ __forceinline__ void se3_invmul(const T* R1, const T* t1, const T* R2, const T* t2, T* R, T* t) {
+PV_HD void se3_invmul(const T* R1, const T* t1, const T* R2, const T* t2, T* R, T* t) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -245,7 +262,7 @@ __host__ __device__ constexpr int pidx(int r, int c) { return r >= c ? r * (r + 
 // In-place Cholesky of a packed N x N SPD matrix: A = L L^T, L packed lower.
 // inv_diag receives 1 / L(j, j). Returns false on a non-positive (or NaN) pivot.
 template <int N, typename T>
-__device__ __forceinline__ bool chol_packed(T* A, T* inv_diag) {
+PV_HD bool chol_packed(T* A, T* inv_diag) {
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
@@ -270,7 +287,7 @@ __device__ __forceinline__ bool chol_packed(T* A, T* inv_diag) {
 
 // Solve L y = b in place (L packed lower from chol_packed).
 template <int N, typename T>
-__device__ __forceinline__ void fwd_solve(const T* L, const T* inv_diag, T* b) {
+PV_HD void fwd_solve(const T* L, const T* inv_diag, T* b) {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         T v = b[i];
@@ -282,7 +299,7 @@ __device__ __forceinline__ void fwd_solve(const T* L, const T* inv_diag, T* b) {
 
 // Solve L^T x = y in place.
 template <int N, typename T>
-__device__ __forceinline__ void bwd_solve(const T* L, const T* inv_diag, T* b) {
+PV_HD void bwd_solve(const T* L, const T* inv_diag, T* b) {
 #pragma unroll
     for (int i = N - 1; i >= 0; --i) {
         T v = b[i];
@@ -295,7 +312,7 @@ __device__ __forceinline__ void bwd_solve(const T* L, const T* inv_diag, T* b) {
 // The same two solves with 1/L_ii stored on the diagonal of L in place of L_ii
 // (a factor whose diagonal is only used through its inverse).
 template <int N, typename T>
-__device__ __forceinline__ void fwd_solve_id(const T* L, T* b) {
+PV_HD void fwd_solve_id(const T* L, T* b) {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         T v = b[i];
@@ -305,7 +322,7 @@ __device__ __forceinline__ void fwd_solve_id(const T* L, T* b) {
     }
 }
 template <int N, typename T>
-__device__ __forceinline__ void bwd_solve_id(const T* L, T* b) {
+PV_HD void bwd_solve_id(const T* L, T* b) {
 #pragma unroll
     for (int i = N - 1; i >= 0; --i) {
         T v = b[i];

@@ -161,13 +161,17 @@ class Tracker:
         return n.value
 
     # --- adjoint ---------------------------------------------------------
-    def set_recording(self, max_iters: int, checkpoint_every: int = 5):
-        """Record target frames (up to max_iters sweeps) for backward()."""
+    def set_recording(self, max_iters: int, checkpoint_every: int = 5, method: int = 0):
+        """Record target frames (up to max_iters sweeps) for backward(); method
+        ADJOINT_HANDWRITTEN (0, default) or ADJOINT_TAPE (1, the FP64 tape kept
+        for cross-checks)."""
         torch = self._torch
+        nat.check(nat.lib.pixvod_set_backward_method(self._h, int(method)), "pixvod_set_backward_method")
         need = ctypes.c_size_t(0)
-        nat.check(nat.lib.pixvod_backward_workspace_bytes(ctypes.byref(self.K), ctypes.byref(self.params),
-                                                          int(max_iters), int(checkpoint_every), ctypes.byref(need)),
-                  "pixvod_backward_workspace_bytes")
+        query = (nat.lib.pixvod_backward_tape_workspace_bytes if method == nat.ADJOINT_TAPE
+                 else nat.lib.pixvod_backward_workspace_bytes)
+        nat.check(query(ctypes.byref(self.K), ctypes.byref(self.params), int(max_iters), int(checkpoint_every),
+                        ctypes.byref(need)), "pixvod_backward_workspace_bytes")
         self._rec = torch.empty(need.value + 256, dtype=torch.uint8, device=self.device)
         ptr = (self._rec.data_ptr() + 255) // 256 * 256
         nat.check(nat.lib.pixvod_set_recording(self._h, ptr, need.value, int(max_iters), int(checkpoint_every)),
@@ -193,9 +197,13 @@ class Tracker:
         g_Is = torch.empty(H, W, **f64)
         g_It = torch.empty(H, W, **f64)
         check = (ctypes.c_double * 2)()
-        nat.check(nat.lib.pixvod_backward(self._h, _ptr(gx), _ptr(gi), g_sig.data_ptr(), g_Is.data_ptr(),
-                                          g_It.data_ptr(), ctypes.cast(check, ctypes.c_void_p)), "pixvod_backward")
-        return {"sigma_D": g_sig[0], "sigma_N": g_sig[1], "I_s": g_Is, "I_t": g_It,
+        st = nat.lib.pixvod_backward(self._h, _ptr(gx), _ptr(gi), g_sig.data_ptr(), g_Is.data_ptr(),
+                                     g_It.data_ptr(), ctypes.cast(check, ctypes.c_void_p))
+        if st not in (nat.OK, nat.ENUMERIC):
+            nat.check(st, "pixvod_backward")
+        # ENUMERIC: a tape overflowed or the recomputed update differs from the
+        # forward's beyond the documented bound; the caller decides
+        return {"sigma_D": g_sig[0], "sigma_N": g_sig[1], "I_s": g_Is, "I_t": g_It, "status": st,
                 "recompute_mismatch": check[0], "tape_nodes": int(check[1])}
 
 
