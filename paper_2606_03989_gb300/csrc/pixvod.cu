@@ -485,6 +485,7 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
     double* dparam = misc;                                                        // 3 doubles
     unsigned long long* mism = reinterpret_cast<unsigned long long*>(misc + 4);  // 1
     unsigned* fl = reinterpret_cast<unsigned*>(misc + 5);                        // flags, max nodes
+    double* scale = misc + 8;  // exponent of the adjoint state's units, max |adjoint| (2 doubles)
     pixvod_status s = cuda_status(sweep_attributes<T>());
     if (s == PIXVOD_OK) s = cuda_status(cudaMemsetAsync(dIs, 0, npx * sizeof(double), st));
     if (s == PIXVOD_OK) s = cuda_status(cudaMemsetAsync(dIt, 0, npx * sizeof(double), st));
@@ -546,6 +547,8 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
     A.tape.adj = reinterpret_cast<double*>(rw + R.off_tadj);
     A.tape.cap = kTapeCap;
     A.tape.n_slots = R.slots;
+    A.scale = scale;
+    const size_t adj_elems = (size_t)n_tiles * pv::TILE_WORDS;
     // the prior mean of the segment the frame was tracked in
     double d_prior = 0.0;
     s = cuda_status(cudaMemcpyAsync(&d_prior, &scalars(h)->d_prior, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -570,10 +573,20 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
             A.adj_in = adj[a ^ 1];
             A.br = brbuf(j);
             if ((s = cuda_status(cudaMemsetAsync(adj[a ^ 1], 0, R.adj_bytes, st))) != PIXVOD_OK) return s;
-            h->launches++;
-            s = tape ? cuda_status(pv::launch_adjoint_sweep(A, R.slots / pv::ad::ADJ_THREADS, st))
-                     : cuda_status(pv::launch_adjoint_hw(A, n_tiles, st));
-            if (s != PIXVOD_OK) return s;
+            if (tape) {
+                h->launches++;
+                if ((s = cuda_status(pv::launch_adjoint_sweep(A, R.slots / pv::ad::ADJ_THREADS, st))) != PIXVOD_OK)
+                    return s;
+            } else {
+                // rescale by a power of two: max |adj_out|, the pass, the new exponent
+                if ((s = cuda_status(cudaMemsetAsync(scale + 1, 0, sizeof(double), st))) != PIXVOD_OK) return s;
+                h->launches += 3;
+                if ((s = cuda_status(pv::launch_adjoint_absmax(adj[a], adj_elems, adj64 ? 1 : 0, scale, st))) !=
+                    PIXVOD_OK)
+                    return s;
+                if ((s = cuda_status(pv::launch_adjoint_hw(A, n_tiles, st))) != PIXVOD_OK) return s;
+                if ((s = cuda_status(pv::launch_adjoint_exponent(scale, st))) != PIXVOD_OK) return s;
+            }
             a ^= 1;
         }
     }

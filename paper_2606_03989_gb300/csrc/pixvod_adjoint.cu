@@ -31,6 +31,8 @@ struct KernelIO {
     size_t si, sj[4];
     int tx[4], ty[4];
     T Is, tapv[12];
+    T in_scale;        // 2^-e: adj_out is read in units of 2^(E + e)
+    double out_scale;  // 2^(E + e): the FP64 gradients' factor
     double mm, dIs, lamD, isD, lamN;
 
     __device__ T mu(int q) const { return Sin[si + q * TILE_PX]; }
@@ -39,7 +41,7 @@ struct KernelIO {
     __device__ T nb(int k, int q) const { return Sin[sj[k] + nb_plane(q, k) * TILE_PX]; }
     __device__ T I_s() const { return Is; }
     __device__ T tap(int q) const { return tapv[q]; }
-    __device__ T ybar(int q) const { return Ao[si + q * TILE_PX]; }
+    __device__ T ybar(int q) const { return Ao[si + q * TILE_PX] * in_scale; }
     __device__ void out(int q, T y, T scale) {
         const double ref = double(Sout[si + q * TILE_PX]);
         const double e = fabs(double(y) - ref) / fmax(double(scale), fabs(ref));
@@ -49,25 +51,25 @@ struct KernelIO {
     __device__ void add_msg(int k, int q, T v) { atomicAdd(Ai + si + (PL_ID + ID_STRIDE * k + q) * TILE_PX, v); }
     __device__ void add_nm(int q, T v) { atomicAdd(Ai + si + (PL_NM + q) * TILE_PX, v); }
     __device__ void add_nb(int k, int q, T v) { atomicAdd(Ai + sj[k] + nb_plane(q, k) * TILE_PX, v); }
-    __device__ void add_Is(T v) { dIs += double(v); }
+    __device__ void add_Is(T v) { dIs += double(v) * out_scale; }
     // taps 0-3 of I_t directly; 4-7 of g_x and 8-11 of g_y through the central
     // differences of the target ingest (replicated borders)
     __device__ void add_tap(int q, T v) {
         const int m = q >> 2, xq = tx[q & 3], yq = ty[q & 3];
         const size_t row = (size_t)yq * W;
+        const double g = double(v) * out_scale;
         if (m == 0) {
-            atomicAdd(dI_t + row + xq, double(v));
+            atomicAdd(dI_t + row + xq, g);
         } else if (m == 1) {
             scatter_gradient_tap(dI_t, W, (int)(row + (xq > 0 ? xq - 1 : 0)), (int)(row + (xq + 1 < W ? xq + 1 : W - 1)),
-                                 double(v));
+                                 g);
         } else {
-            scatter_gradient_tap(dI_t, W, (yq > 0 ? yq - 1 : 0) * W + xq, (yq + 1 < H ? yq + 1 : H - 1) * W + xq,
-                                 double(v));
+            scatter_gradient_tap(dI_t, W, (yq > 0 ? yq - 1 : 0) * W + xq, (yq + 1 < H ? yq + 1 : H - 1) * W + xq, g);
         }
     }
-    __device__ void add_lamD(T v) { lamD += double(v); }
-    __device__ void add_isD(T v) { isD += double(v); }
-    __device__ void add_lamN(T v) { lamN += double(v); }
+    __device__ void add_lamD(T v) { lamD += double(v) * out_scale; }
+    __device__ void add_isD(T v) { isD += double(v) * out_scale; }
+    __device__ void add_lamN(T v) { lamN += double(v) * out_scale; }
 };
 
 // The hand-written adjoint of one sweep: block = one state tile (32 x 4 pixels),
@@ -98,6 +100,15 @@ __global__ void __launch_bounds__(TILE_PX) k_adjoint_hw(const AdjArgs A) {
         io.H = H;
         io.si = (size_t)tile * TILE_WORDS + lane;
         io.mm = io.dIs = io.lamD = io.isD = io.lamN = 0.0;
+        // the adjoint state is rescaled by a power of two before every pass: the
+        // unrolled derivative can grow by many orders of magnitude over the sweeps,
+        // beyond the float range, while the pass is linear in its input
+        {
+            const double mx = A.scale[1];
+            const int e = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) : 0;
+            io.in_scale = T(ldexp(1.0, -e));
+            io.out_scale = ldexp(1.0, (int)A.scale[0] + e);
+        }
         const size_t ii = (size_t)v * g.pitch + u;
         hw::PixCtx<T> c;
         c.u = T(u);
@@ -184,7 +195,37 @@ __global__ void __launch_bounds__(TILE_PX) k_adjoint_hw(const AdjArgs A) {
     if (lane < 3 && red[lane] != 0.0) atomicAdd(A.dparam + lane, red[lane]);
 }
 
+template <typename T>
+__global__ void k_adjoint_absmax(const T* __restrict__ a, size_t n, unsigned long long* __restrict__ mx) {
+    double m = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double x = fabs(double(a[i]));
+        if (isfinite(x) && x > m) m = x;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_nonneg(mx, m);
+}
+
+__global__ void k_adjoint_exponent(double* scale) {
+    const double mx = scale[1];
+    scale[0] += (mx > 0.0 && isfinite(mx)) ? double(ilogb(mx)) : 0.0;
+}
+
 }  // namespace
+
+cudaError_t launch_adjoint_absmax(const void* a, size_t n, int adj64, double* scale, cudaStream_t st) {
+    unsigned long long* mx = reinterpret_cast<unsigned long long*>(scale + 1);
+    if (adj64)
+        k_adjoint_absmax<double><<<1024, 256, 0, st>>>(static_cast<const double*>(a), n, mx);
+    else
+        k_adjoint_absmax<float><<<1024, 256, 0, st>>>(static_cast<const float*>(a), n, mx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_exponent(double* scale, cudaStream_t st) {
+    k_adjoint_exponent<<<1, 1, 0, st>>>(scale);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_adjoint_sweep(const AdjArgs& A, int blocks, cudaStream_t st) {
     k_adjoint_sweep<<<blocks, ad::ADJ_THREADS, 0, st>>>(A);

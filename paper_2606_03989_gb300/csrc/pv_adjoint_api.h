@@ -49,6 +49,11 @@ struct AdjArgs {
     unsigned* max_nodes;           // longest tape of a pixel
     unsigned* flags;
     ad::TapeCtl tape;
+    // hand-written pass: scale[0] = E, the adjoint state holds values in units
+    // of 2^E; scale[1] = max |adj_out| in those units (as written by
+    // launch_adjoint_absmax); the pass reads adj_out times 2^-e with
+    // e = ilogb(scale[1]), so its adj_in is in units of 2^(E + e)
+    double* scale;
 };
 
 // adjoint of one sweep by the reverse-mode tape (FP64), `blocks` blocks of
@@ -62,6 +67,10 @@ cudaError_t launch_adjoint_hw(const AdjArgs& A, int n_tiles, cudaStream_t st);
 // (adj64) or FP32
 cudaError_t launch_adjoint_seed(const AdjArgs& A, const double* grad_xi, const double* grad_invdepth, void* adj,
                                 int adj64, cudaStream_t st);
+// scale[1] = max |a[i]| over n elements (finite values; scale[1] must be 0 before)
+cudaError_t launch_adjoint_absmax(const void* a, size_t n, int adj64, double* scale, cudaStream_t st);
+// scale[0] += ilogb(scale[1]): the units of the adjoint state after a hand-written pass
+cudaError_t launch_adjoint_exponent(double* scale, cudaStream_t st);
 // dL/d(sigma_D, sigma_N) from the adjoints of lam_D, 1/sigma_D and lam_N
 cudaError_t launch_sigma_grads(const double* dparam, double sigma_D, double sigma_N, double* out, cudaStream_t st);
 

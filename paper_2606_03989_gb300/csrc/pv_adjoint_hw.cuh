@@ -169,44 +169,50 @@ namespace hw {
 // ---------------------------------------------------------------------------
 // local Jacobians of Exp and Log, contracted with an adjoint
 // ---------------------------------------------------------------------------
-// xi_bar += (d(R, t)/d xi)^T (R_bar, t_bar) at xi
+// xi_bar += (d(R, t)/d xi)^T (R_bar, t_bar) at xi. R depends on theta only and
+// t = V(theta) rho, so forward-mode tangents are needed in theta alone:
+// rho_bar = V^T t_bar.
 template <typename T>
 PV_HD void exp_vjp(const T* xi, const T* Rb, const T* tb, T* xib) {
-    typedef Dual<T, 6> D;
-    D x[6], R[9], t[3];
+    typedef Dual<T, 3> D;
+    D x[6], R[9], t[3], V[9];
     for (int k = 0; k < 6; ++k) {
         x[k] = D(0.0);
         x[k].v = xi[k];
-        x[k].d[k] = T(1);
+        if (k < 3) x[k].d[k] = T(1);
     }
-    se3_exp(x, R, t);
-    for (int k = 0; k < 6; ++k) {
+    se3_exp_V(x, R, t, V);
+    for (int k = 0; k < 3; ++k) {
         T acc = T(0);
         for (int q = 0; q < 9; ++q) acc += Rb[q] * R[q].d[k];
         for (int q = 0; q < 3; ++q) acc += tb[q] * t[q].d[k];
         xib[k] += acc;
     }
+    for (int k = 0; k < 3; ++k) xib[3 + k] += V[k].v * tb[0] + V[3 + k].v * tb[1] + V[6 + k].v * tb[2];
 }
 
-// (R_bar, t_bar) += (d xi / d(R, t))^T xi_bar for xi = Log(R, t)
+// (R_bar, t_bar) += (d xi / d(R, t))^T xi_bar for xi = Log(R, t). The Log
+// depends on R only through w = vee(R - R^T)/2 and c = (tr R - 1)/2, and
+// rho = V^-1(theta) t, so forward-mode tangents are needed in (w, c) alone:
+// t_bar = V^-T rho_bar.
 template <typename T>
 PV_HD void log_vjp(const T* R, const T* t, const T* xb, T* Rb, T* tb) {
-    typedef Dual<T, 7> D;
-    D in[7], tt[3], x[6];
-    const T w0 = T(0.5) * (R[7] - R[5]), w1 = T(0.5) * (R[2] - R[6]), w2 = T(0.5) * (R[3] - R[1]);
-    const T c = T(0.5) * (R[0] + R[4] + R[8] - T(1));
-    const T vals[7] = {w0, w1, w2, c, t[0], t[1], t[2]};
-    for (int k = 0; k < 7; ++k) {
+    typedef Dual<T, 4> D;
+    D in[4], tt[3], x[6], Vi[9];
+    const T vals[4] = {T(0.5) * (R[7] - R[5]), T(0.5) * (R[2] - R[6]), T(0.5) * (R[3] - R[1]),
+                       T(0.5) * (R[0] + R[4] + R[8] - T(1))};
+    for (int k = 0; k < 4; ++k) {
         in[k] = D(0.0);
         in[k].v = vals[k];
         in[k].d[k] = T(1);
     }
-    tt[0] = in[4];
-    tt[1] = in[5];
-    tt[2] = in[6];
-    se3_log_wct(in[0], in[1], in[2], in[3], tt, x);
-    T g[7];
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < 3; ++k) {
+        tt[k] = D(0.0);
+        tt[k].v = t[k];
+    }
+    se3_log_wct(in[0], in[1], in[2], in[3], tt, x, Vi);
+    T g[4];
+    for (int k = 0; k < 4; ++k) {
         T acc = T(0);
         for (int q = 0; q < 6; ++q) acc += xb[q] * x[q].d[k];
         g[k] = acc;
@@ -221,9 +227,7 @@ PV_HD void log_vjp(const T* R, const T* t, const T* xb, T* Rb, T* tb) {
     Rb[0] += T(0.5) * g[3];
     Rb[4] += T(0.5) * g[3];
     Rb[8] += T(0.5) * g[3];
-    tb[0] += g[4];
-    tb[1] += g[5];
-    tb[2] += g[6];
+    for (int k = 0; k < 3; ++k) tb[k] += Vi[k].v * xb[3] + Vi[3 + k].v * xb[4] + Vi[6 + k].v * xb[5];
 }
 
 // ---------------------------------------------------------------------------

@@ -178,8 +178,9 @@ PV_HD void so3_poly(const T* w, T a, T b, T* M) {
 // Exp: xi (6) -> R (9), t (3). Below ab_series_max the coefficients come from
 // their power series in t^2, so small rotations take no square root, division
 // or trigonometric call.
+// Exp with V(theta) (t = V rho) returned as well (the adjoint uses it)
 template <typename T>
-PV_HD void se3_exp(const T* xi, T* R, T* t) {
+PV_HD void se3_exp_V(const T* xi, T* R, T* t, T* V) {
     T t2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
     T A, B, C;
     if (t2 < Prec<T>::ab_series_max * Prec<T>::ab_series_max) {
@@ -191,9 +192,14 @@ PV_HD void se3_exp(const T* xi, T* R, T* t) {
         C = coef_C(th, A);
     }
     so3_poly(xi, A, B, R);
-    T V[9];
     so3_poly(xi, B, C, V);
     mat3_vec(V, xi + 3, t);
+}
+
+template <typename T>
+PV_HD void se3_exp(const T* xi, T* R, T* t) {
+    T V[9];
+    se3_exp_V(xi, R, t, V);
 }
 
 // Log: R (9), t (3) -> xi (6); rotation angles below pi. With w = vee(R - R^T)/2,
@@ -204,7 +210,7 @@ PV_HD void se3_exp(const T* xi, T* R, T* t) {
 // The logarithm from w = vee(R - R^T)/2, c = (tr R - 1)/2 and t (se3_log below
 // computes w and c; the adjoint differentiates this part in w, c and t).
 template <typename T>
-PV_HD void se3_log_wct(T w0, T w1, T w2, T c, const T* t, T* xi) {
+PV_HD void se3_log_wct(T w0, T w1, T w2, T c, const T* t, T* xi, T* Vi) {
     static_assert(Prec<T>::asin_series_max <= Prec<T>::d_series_max / 2, "series D range");
     T s2 = w0 * w0 + w1 * w1 + w2 * w2;
     T ratio, D;
@@ -221,15 +227,15 @@ PV_HD void se3_log_wct(T w0, T w1, T w2, T c, const T* t, T* xi) {
     xi[0] = w0 * ratio;
     xi[1] = w1 * ratio;
     xi[2] = w2 * ratio;
-    T Vi[9];
     so3_poly(xi, T(-0.5), D, Vi);
     mat3_vec(Vi, t, xi + 3);
 }
 
 template <typename T>
 PV_HD void se3_log(const T* R, const T* t, T* xi) {
+    T Vi[9];
     se3_log_wct(T(0.5) * (R[7] - R[5]), T(0.5) * (R[2] - R[6]), T(0.5) * (R[3] - R[1]),
-                T(0.5) * (R[0] + R[4] + R[8] - T(1)), t, xi);
+                T(0.5) * (R[0] + R[4] + R[8] - T(1)), t, xi, Vi);
 }
 
 // (R1, t1) * (R2, t2)
