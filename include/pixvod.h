@@ -59,6 +59,15 @@ typedef enum {
 #define PIXVOD_FLAG_NONPOS_PIVOT 0x1u /* a Cholesky pivot was <= 0; that pixel skipped its update */
 #define PIXVOD_FLAG_NONFINITE    0x2u /* a non-finite mean was produced */
 #define PIXVOD_FLAG_TIMEOUT      0x4u /* a bounded spin-wait gave up */
+#define PIXVOD_FLAG_BOUNDS       0x10u /* checked build only: an index left its buffer (access skipped) */
+
+/* Checked build. libpixvod_checked.so is the same library compiled with
+ * PIXVOD_CHECKED: every index the sweep computes (neighbour state, input
+ * planes, bilinear taps, shared-memory message slots) is tested against its
+ * buffer, a violation sets PIXVOD_FLAG_BOUNDS and skips the access (nothing
+ * traps), and the lanes of ragged state tiles outside the image are filled with
+ * NaN at creation so that any read of them shows as PIXVOD_FLAG_NONFINITE. It is
+ * meant for tests; results can differ from the plain build by FP32 rounding. */
 
 /* Pinhole intrinsics (Eq. 2): pixel centres at integer coordinates. */
 typedef struct {

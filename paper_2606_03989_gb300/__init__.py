@@ -11,7 +11,7 @@ import importlib
 _NATIVE = {"ADJOINT_HANDWRITTEN", "ADJOINT_TAPE", "ECUDA", "EINVAL", "ENOMEM", "ENUMERIC", "ESTATE", "ETIMEOUT", "FLAG_NONFINITE",
            "SCHED_PLAIN", "SCHED_BATCHED", "SCHED_PERSISTENT", "SCHED_NAMES",
            "TOPOLOGY_GRID", "TOPOLOGY_QUADTREE", "pixvod_intrinsics",
-           "FLAG_NONPOS_PIVOT", "FLAG_TIMEOUT", "LIB_PATH", "OK", "PixvodError", "StateView",
+           "FLAG_NONPOS_PIVOT", "FLAG_TIMEOUT", "FLAG_BOUNDS", "LIB_PATH", "OK", "PixvodError", "StateView",
            "intrinsics", "lib", "params", "params_default", "parse_state", "status_string",
            "workspace_bytes"}
 

@@ -14,14 +14,16 @@ from typing import Optional
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "lib", "libpixvod.so")
+# PIXVOD_LIBRARY=checked selects the checked build (lib/libpixvod_checked.so)
+LIB_PATH = os.path.join(_PKG, "lib", "libpixvod_checked.so" if os.environ.get("PIXVOD_LIBRARY") == "checked"
+                        else "libpixvod.so")
 
 OK, EINVAL, ECUDA, ENUMERIC, ESTATE, ETIMEOUT, ENOMEM = range(7)
 TOPOLOGY_GRID, TOPOLOGY_QUADTREE = 0, 1
 SCHED_PLAIN, SCHED_BATCHED, SCHED_PERSISTENT = 0, 1, 2
 SCHED_NAMES = {SCHED_PLAIN: "plain", SCHED_BATCHED: "batched", SCHED_PERSISTENT: "persistent"}
 ADJOINT_HANDWRITTEN, ADJOINT_TAPE = 0, 1
-FLAG_NONPOS_PIVOT, FLAG_NONFINITE, FLAG_TIMEOUT = 0x1, 0x2, 0x4
+FLAG_NONPOS_PIVOT, FLAG_NONFINITE, FLAG_TIMEOUT, FLAG_BOUNDS = 0x1, 0x2, 0x4, 0x10
 N_PLANES = 151
 N_INPUT_PLANES = 6
 PL_MU, PL_MP, PL_U, PL_S, PL_ID, ID_STRIDE, PL_NM = 0, 7, 28, 34, 35, 27, 143

@@ -2,8 +2,11 @@
 
     python -m paper_2606_03989_gb300.build [--verbose-ptxas]
 
-Produces paper_2606_03989_gb300/lib/libpixvod.so (git-ignored). The library
-links the CUDA runtime statically and has no dependency on PyTorch.
+Produces paper_2606_03989_gb300/lib/libpixvod.so and its checked variant
+lib/libpixvod_checked.so (compiled with PIXVOD_CHECKED: bounds-checked indices,
+NaN in the out-of-image lanes of ragged tiles; for tests), both git-ignored.
+The libraries link the CUDA runtime statically and have no dependency on
+PyTorch.
 """
 from __future__ import annotations
 
@@ -17,6 +20,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libpixvod.so")
+LIB_CHECKED = os.path.join(LIBDIR, "libpixvod_checked.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -32,42 +36,50 @@ def sources():
 
 
 def build(verbose_ptxas: bool = False, force: bool = False) -> str:
+    """Build both libraries (the plain one and the checked one) if any source is
+    newer; returns the plain library's path."""
     os.makedirs(LIBDIR, exist_ok=True)
     deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     deps.append(os.path.join(ROOT, "include", "pixvod.h"))
-    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in deps):
+    targets = [(LIB, []), (LIB_CHECKED, ["-DPIXVOD_CHECKED"])]
+    stale = [(lib, flags) for lib, flags in targets
+             if force or not os.path.exists(lib) or any(os.path.getmtime(lib) < os.path.getmtime(d) for d in deps)]
+    if not stale:
         return LIB
-    tmp = LIB + ".tmp.%d" % os.getpid()
     nvcc = nvcc_path()
-    # one object per translation unit, compiled in parallel, then one link
-    objs, procs = [], []
-    for src in sources():
-        obj = os.path.join(LIBDIR, os.path.basename(src) + ".%d.o" % os.getpid())
-        cmd = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c",
-               "-I", os.path.join(ROOT, "include"), "-o", obj, src]
-        if verbose_ptxas:
-            cmd += ["-Xptxas", "-v"]
-        objs.append(obj)
-        procs.append(subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    # one object per translation unit and library, all compiled in parallel, then one link each
+    jobs = []
+    for lib, flags in stale:
+        for src in sources():
+            obj = os.path.join(LIBDIR, "%s.%s.%d.o" % (os.path.basename(lib), os.path.basename(src), os.getpid()))
+            cmd = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c",
+                   "-I", os.path.join(ROOT, "include"), "-o", obj, src] + flags
+            if verbose_ptxas and not flags:
+                cmd += ["-Xptxas", "-v"]
+            jobs.append((lib, src, obj, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                                         text=True)))
     errors, logs = [], []
-    for src, pr in zip(sources(), procs):
+    for lib, src, obj, pr in jobs:
         out, err = pr.communicate()
         logs.append(err)
         if pr.returncode != 0:
-            errors.append("%s:\n%s%s" % (src, out, err))
+            errors.append("%s (%s):\n%s%s" % (src, os.path.basename(lib), out, err))
     try:
         if errors:
             raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-        res = subprocess.run([nvcc, ARCH, "-shared", "-o", tmp] + objs, capture_output=True, text=True)
-        if res.returncode != 0:
-            raise RuntimeError("nvcc link failed:\n" + res.stdout + res.stderr)
+        for lib, _ in stale:
+            tmp = lib + ".tmp.%d" % os.getpid()
+            objs = [obj for l2, _, obj, _ in jobs if l2 == lib]
+            res = subprocess.run([nvcc, ARCH, "-shared", "-o", tmp] + objs, capture_output=True, text=True)
+            if res.returncode != 0:
+                raise RuntimeError("nvcc link failed:\n" + res.stdout + res.stderr)
+            os.replace(tmp, lib)
     finally:
-        for obj in objs:
+        for _, _, obj, _ in jobs:
             if os.path.exists(obj):
                 os.remove(obj)
     if verbose_ptxas:
         sys.stderr.write("".join(logs))
-    os.replace(tmp, LIB)
     return LIB
 
 

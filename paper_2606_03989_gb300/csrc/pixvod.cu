@@ -10,6 +10,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pixvod.h"
 #include "pv_adjoint_api.h"
 #include "pv_batch.cuh"
@@ -20,6 +22,13 @@ using pv::Geometry;
 using pv::Scalars;
 
 namespace {
+
+// NVTX range around a library call (visible in profilers; header-only NVTX, a
+// no-op when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 constexpr int kPitchAlign = 32;       // elements per row rounded up to 32
 constexpr size_t kAlign = 256;        // every workspace region starts on 256 bytes
@@ -321,6 +330,26 @@ void harvest_profile(pixvod_handle* h) {
 }
 
 bool is_quadtree(const pixvod_handle* h) { return h->L.q.n_levels > 0; }
+
+// checked builds: NaN in the out-of-image lanes of both state buffers
+pixvod_status poison_outside(pixvod_handle* h) {
+#ifdef PIXVOD_CHECKED
+    const int n_tiles = h->L.tiles_x * h->L.tiles_y;
+    for (int b = 0; b < 2; ++b) {
+        if (h->p.precision == 64)
+            pv::k_poison_outside<double><<<n_tiles, pv::TILE_PX, 0, h->stream>>>(
+                geometry<double>(h), n_tiles, reinterpret_cast<double*>(h->ws + h->L.off_state[b]));
+        else
+            pv::k_poison_outside<float><<<n_tiles, pv::TILE_PX, 0, h->stream>>>(
+                geometry<float>(h), n_tiles, reinterpret_cast<float*>(h->ws + h->L.off_state[b]));
+        pixvod_status s = cuda_status(cudaGetLastError());
+        if (s != PIXVOD_OK) return s;
+    }
+#else
+    (void)h;
+#endif
+    return PIXVOD_OK;
+}
 
 template <typename T>
 T* node_ptr(pixvod_handle* h, int b) {
@@ -742,6 +771,7 @@ pixvod_status pixvod_create(const pixvod_intrinsics* K, const pixvod_params* p, 
         if (s == PIXVOD_OK)
             s = cuda_status(cudaMemcpyAsync(sc->T_cur, eye, sizeof(eye), cudaMemcpyHostToDevice, h->stream));
         if (s == PIXVOD_OK) s = upload_desc(h);
+        if (s == PIXVOD_OK) s = poison_outside(h);
         if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(h->stream));
     }
     if (s != PIXVOD_OK) {
@@ -760,6 +790,7 @@ pixvod_status pixvod_destroy(pixvod_handle* h) {
 }
 
 pixvod_status pixvod_track(pixvod_handle* h, const float* d_frame, const float* d_normals, int32_t n_iters) {
+    NvtxRange nvtx_range("pixvod_track");
     if (!h || !d_frame || n_iters < 0 || !aligned(d_frame, 4) || (d_normals && !aligned(d_normals, 4)))
         return PIXVOD_EINVAL;
     const bool needs_normals =
@@ -789,6 +820,7 @@ pixvod_status pixvod_track_host(pixvod_handle* h, const float* h_frame, const fl
 }
 
 pixvod_status pixvod_sweep(pixvod_handle* h, int32_t n_iters) {
+    NvtxRange nvtx_range("pixvod_sweep");
     if (!h || n_iters < 0) return PIXVOD_EINVAL;
     if (!h->has_target) return PIXVOD_ESTATE;
     pixvod_status s;
@@ -1043,6 +1075,7 @@ pixvod_status pixvod_set_backward_window(pixvod_handle* h, int32_t last_sweeps) 
 
 pixvod_status pixvod_backward(pixvod_handle* h, const double* d_grad_xi, const double* d_grad_invdepth,
                               double* d_grad_sigmas, double* d_grad_Is, double* d_grad_It, double* check) {
+    NvtxRange nvtx_range("pixvod_backward");
     if (!h || !d_grad_sigmas || !d_grad_Is || !d_grad_It) return PIXVOD_EINVAL;
     if (!h->rec_ws || !h->rec_valid) return PIXVOD_ESTATE;
     return h->p.precision == 64
@@ -1367,6 +1400,7 @@ pixvod_status pixvod_batch_create(int32_t n, const pixvod_intrinsics* K, const p
         if (s == PIXVOD_OK)
             s = cuda_status(cudaMemcpyAsync(sc->T_cur, eye, sizeof(eye), cudaMemcpyHostToDevice, b->stream));
         if (s == PIXVOD_OK) s = upload_desc(&b->seq[i]);  // for the plain schedule
+        if (s == PIXVOD_OK) s = poison_outside(&b->seq[i]);
         if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(b->stream));  // eye outlives the copies
     }
     if (s == PIXVOD_OK) {
@@ -1407,6 +1441,7 @@ pixvod_status pixvod_batch_set_inputs(pixvod_batch* b, const float* const* d_fra
 }
 
 pixvod_status pixvod_batch_track(pixvod_batch* b, int32_t n_iters) {
+    NvtxRange nvtx_range("pixvod_batch_track");
     if (!b || n_iters < 0) return PIXVOD_EINVAL;
     if (!b->inputs_set) return PIXVOD_ESTATE;
     return b->p.precision == 64 ? batch_track_impl<double>(b, n_iters) : batch_track_impl<float>(b, n_iters);
@@ -1470,6 +1505,7 @@ pixvod_status pixvod_batch_get_schedule(pixvod_batch* b, int32_t* schedule, int3
 }
 
 pixvod_status pixvod_batch_autotune(pixvod_batch* b, int32_t n_iters, int32_t reps, float* times_ms) {
+    NvtxRange nvtx_range("pixvod_batch_autotune");
     if (!b || n_iters < 1 || reps < 1) return PIXVOD_EINVAL;
     if (!b->inputs_set || b->frame_index != 1) return PIXVOD_ESTATE;
     return b->p.precision == 64 ? batch_autotune_impl<double>(b, n_iters, reps, times_ms)

@@ -49,6 +49,17 @@ constexpr int TILE_WORDS = N_PLANES * TILE_PX;
 constexpr unsigned FLAG_NONPOS_PIVOT = 0x1u;
 constexpr unsigned FLAG_NONFINITE = 0x2u;
 constexpr unsigned FLAG_TIMEOUT = 0x4u;
+constexpr unsigned FLAG_BOUNDS = 0x10u;  // checked builds: an index left its buffer (access skipped)
+
+// Checked builds (PIXVOD_CHECKED): every computed index of the sweep (neighbour
+// state, input planes, bilinear taps, shared-memory message slots) is tested
+// against its buffer; a violation sets FLAG_BOUNDS in *flags and yields
+// `fallback` (0) so the access is skipped. Plain builds compile the index as is.
+#ifdef PIXVOD_CHECKED
+#define PV_IDX(idx, limit, flags) (((size_t)(idx) < (size_t)(limit)) ? (size_t)(idx) : ((flags) |= FLAG_BOUNDS, (size_t)0))
+#else
+#define PV_IDX(idx, limit, flags) ((size_t)(idx))
+#endif
 
 // Device-resident per-handle scalars (doubles, fixed layout; the checkpoint
 // format copies the first 40).
@@ -183,6 +194,18 @@ __device__ __forceinline__ void reset_px(const Geometry<T>& g, const Factors<T>&
     st[PL_S * TILE_PX] = f.lam_Z;
 }
 
+// Checked builds: the lanes of ragged tiles that lie outside the image hold NaN
+// in every plane, so that any computation reading them shows as FLAG_NONFINITE.
+template <typename T>
+__global__ void k_poison_outside(Geometry<T> g, int n_tiles, T* state) {
+    const int tile = blockIdx.x, lane = threadIdx.x;
+    const int u = (tile % g.tiles_x) * TILE_W + lane % TILE_W;
+    const int v = (tile / g.tiles_x) * TILE_H + lane / TILE_W;
+    if (tile >= n_tiles || (u < g.W && v < g.H)) return;
+    T* st = state + (size_t)tile * TILE_WORDS + lane;
+    for (int p = 0; p < N_PLANES; ++p) st[p * TILE_PX] = T(NAN);
+}
+
 template <typename T>
 __global__ void k_reset(Geometry<T> g, Factors<T> f, T* state, const Scalars* sc) {
     int u = blockIdx.x * blockDim.x + threadIdx.x;
@@ -277,9 +300,14 @@ __device__ __forceinline__ bool sweep_pixel(const SweepArgs<T>& a, int tx, int t
     const Factors<T>& F = a.f;
     const size_t tile = (size_t)ty * g.tiles_x + tx;
     if (u >= g.W || v >= g.H) return true;
-    const int i = v * g.pitch + u;
-    const T* __restrict__ Si = a.in + tile * TILE_WORDS + tid;   // this pixel, plane 0
-    T* __restrict__ Di = a.out + tile * TILE_WORDS + tid;
+    unsigned flags = 0;
+    const size_t n_state = (size_t)g.tiles_x * ((g.H + TILE_H - 1) / TILE_H) * TILE_WORDS;
+    const size_t n_plane = g.plane;
+    (void)n_state;
+    (void)n_plane;
+    const int i = (int)PV_IDX(v * g.pitch + u, n_plane, flags);
+    const T* __restrict__ Si = a.in + PV_IDX(tile * TILE_WORDS + tid, n_state, flags);   // this pixel, plane 0
+    T* __restrict__ Di = a.out + PV_IDX(tile * TILE_WORDS + tid, n_state, flags);
 
     T xi[6], d;
 #pragma unroll
@@ -309,7 +337,6 @@ __device__ __forceinline__ bool sweep_pixel(const SweepArgs<T>& a, int tx, int t
     eb[6] -= F.lam_Z * (d - T(a.sc->d_prior));
 
     // --- a2/a3: pairwise messages from the four neighbours ---
-    unsigned flags = 0;
     if (!mbar_wait_bounded(bar, parity)) {
         // the tile's messages never arrived: flag it, wait once more, leave the tile
         atomicOr(&a.sc->flags, FLAG_TIMEOUT);
@@ -319,7 +346,7 @@ __device__ __forceinline__ bool sweep_pixel(const SweepArgs<T>& a, int tx, int t
     const T beta = F.beta, omb = T(1) - F.beta;
 #pragma unroll 1
     for (int k = 0; k < 4; ++k) {
-        T* mb = msg + (k * ID_STRIDE) * TILE_PX + tid;          // identity slot k
+        T* mb = msg + PV_IDX((k * ID_STRIDE) * TILE_PX + tid, (MSG_PLANES - ID_STRIDE + 1) * TILE_PX, flags);  // slot k
         const int un = u + (k == 0 ? -1 : (k == 1 ? 1 : 0));
         const int vn = v + (k == 2 ? -1 : (k == 3 ? 1 : 0));
         const bool has = un >= 0 && un < g.W && vn >= 0 && vn < g.H;
@@ -329,7 +356,7 @@ __device__ __forceinline__ bool sweep_pixel(const SweepArgs<T>& a, int tx, int t
             continue;
         }
         const int ko = k ^ 1;
-        const T* Sj = a.in + state_index(un, vn, g.tiles_x);
+        const T* Sj = a.in + PV_IDX(state_index(un, vn, g.tiles_x), n_state, flags);
         // variable-to-factor marginal of j: V = W + u u^T with W = M_p,j - Lambda_{f->j}
         // (pose prior plus j's three other identity messages) and u = u_j, and
         // eta_v = -eta_{f->j}. All of j's loads are issued here, ahead of the Exp/Log
@@ -427,11 +454,12 @@ __device__ __forceinline__ bool sweep_pixel(const SweepArgs<T>& a, int tx, int t
         const int vn = v + (k == 2 ? -1 : (k == 3 ? 1 : 0));
         if (!(un >= 0 && un < g.W && vn >= 0 && vn < g.H)) continue;
         const int ko = k ^ 1;
-        const T* Sj = a.in + state_index(un, vn, g.tiles_x);
+        const T* Sj = a.in + PV_IDX(state_index(un, vn, g.tiles_x), n_state, flags);
         T dj = ld_state(Sj + 6 * TILE_PX);
         T sv = ld_state(Sj + PL_S * TILE_PX) - ld_state(Sj + (PL_NM + 2 * ko) * TILE_PX);
         T evn = -ld_state(Sj + (PL_NM + 2 * ko + 1) * TILE_PX);
-        T m = k == 0 ? a.m_x[i - 1] : (k == 1 ? a.m_x[i] : (k == 2 ? a.m_y[i - g.pitch] : a.m_y[i]));
+        T m = k == 0 ? a.m_x[PV_IDX(i - 1, n_plane, flags)]
+                     : (k == 1 ? a.m_x[i] : (k == 2 ? a.m_y[PV_IDX(i - g.pitch, n_plane, flags)] : a.m_y[i]));
         T sg = (k == 0 || k == 2) ? T(1) : T(-1);
         T rn = d - dj + sg * m;
         T den = v_div(T(1), F.lam_N + sv);
@@ -474,6 +502,12 @@ __device__ __forceinline__ bool sweep_pixel(const SweepArgs<T>& a, int tx, int t
             x0 = min(x0, g.W - 1);
             y0 = min(y0, g.H - 1);
             int x1 = min(x0 + 1, g.W - 1), y1 = min(y0 + 1, g.H - 1);
+#ifdef PIXVOD_CHECKED
+            if (x0 < 0 || y0 < 0 || (size_t)y1 * g.pitch + x1 >= n_plane) {
+                flags |= FLAG_BOUNDS;
+                x0 = y0 = x1 = y1 = 0;
+            }
+#endif
             T ax = x - T(x0), ay = y - T(y0);
             T It = bilinear(a.I_t, g.pitch, x0, y0, x1, y1, ax, ay);
             gx = bilinear(a.g_x, g.pitch, x0, y0, x1, y1, ax, ay);
