@@ -144,7 +144,7 @@ constexpr int kAdjSlotsPerSM = 256;       // adjoint threads per SM (eight block
 struct RecLayout {
     int n_ckpt, every, max_iters, slots;
     size_t state_bytes, adj_bytes, br_bytes;
-    size_t off_ckpt, off_seg, off_br, off_adj[2], off_desc, off_misc, off_par, off_w, off_tadj, total;
+    size_t off_ckpt, off_seg, off_br, off_adj[2], off_scr, off_desc, off_misc, off_par, off_w, off_tadj, total;
 };
 
 RecLayout make_rec_layout(const Layout& L, int max_iters, int every, int n_px, int num_sms, bool tape) {
@@ -169,6 +169,8 @@ RecLayout make_rec_layout(const Layout& L, int max_iters, int every, int n_px, i
         R.off_adj[b] = off;
         off += R.adj_bytes;
     }
+    R.off_scr = off;  // between the stages of the hand-written pass (sized for FP64)
+    off += align_up(pv::adjoint_scratch_bytes(L.tiles_x * L.tiles_y, 1), kAlign);
     R.off_desc = off;
     off += align_up((size_t)max_iters * kDescBytes, kAlign);
     R.off_misc = off;
@@ -613,7 +615,8 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
                 if ((s = cuda_status(pv::launch_adjoint_absmax(adj[a], adj_elems, adj64 ? 1 : 0, scale, st))) !=
                     PIXVOD_OK)
                     return s;
-                if ((s = cuda_status(pv::launch_adjoint_hw(A, n_tiles, st))) != PIXVOD_OK) return s;
+                h->launches += 3;
+                if ((s = cuda_status(pv::launch_adjoint_hw(A, n_tiles, rw + R.off_scr, st))) != PIXVOD_OK) return s;
                 if ((s = cuda_status(pv::launch_adjoint_exponent(scale, st))) != PIXVOD_OK) return s;
             }
             a ^= 1;

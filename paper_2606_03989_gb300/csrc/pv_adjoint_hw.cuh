@@ -287,6 +287,8 @@ constexpr int N_OUT = 151; // output planes, in state order
 //   T nb(k, q)                      neighbour value q (NB_*) of direction k
 //   T I_s(), tap(q)                 source intensity; I_t, g_x, g_y taps (4 each)
 //   T ybar(q)                       adjoint of output plane q (state order)
+//   void identity_forward(k, R, t, L, e)  the damped identity message of
+//                                   direction k (damped_identity, or precomputed)
 //   void out(q, y, scale)           recomputed output plane q and the magnitude
 //                                   of the terms it is formed from (>= 1, >= |y|)
 //   void add_mu/add_msg/add_nm/add_nb/add_Is/add_tap(..., v), add_lamD/add_isD/
@@ -427,10 +429,36 @@ PV_HD void photometric(T d, T I_s, const T* tap, const PixCtx<T>& c, const T* R,
     *rph = P.r;
 }
 
-// The update's outputs (through io.out) and the adjoints of its inputs (through
-// io.add_*) for the output adjoints io.ybar.
+// The damped identity message of direction k into the pixel at pose (R, t):
+// Lambda (packed) and eta, from the neighbour's values and the pixel's old
+// message of slot k (an I/O object's identity_forward may compute it with this,
+// or return it precomputed).
 template <typename T, typename IO>
-PV_HD void pixel_vjp(IO& io, const PixCtx<T>& c) {
+PV_HD void damped_identity(IO& io, const PixCtx<T>& c, int k, const T* R, const T* t, T* L, T* e) {
+    const T beta = c.beta, omb = T(1) - c.beta;
+    T nbk[NB_VALS];
+    for (int q = 0; q < NB_VALS; ++q) nbk[q] = io.nb(k, q);
+    T rb[6], W[21], Lc[21], z[6], iuz, Ln[21], en[6];
+    identity_message(nbk, R, t, c.lam_R, rb, W, Lc, z, &iuz, Ln, en);
+    for (int q = 0; q < 6; ++q) e[q] = omb * en[q] + beta * io.msg(k, 21 + q);
+    for (int q = 0; q < 21; ++q) L[q] = omb * Ln[q] + beta * io.msg(k, q);
+}
+
+// What the main stage of the reverse pass hands to the per-direction and pose
+// stages: the adjoints of the four damped identity messages (Lambda packed, eta),
+// of the pixel's rotation and translation (R, t = Exp(xi)), of xi through the
+// prior, and of the log-depth.
+template <typename T>
+struct MainOut {
+    T Lb[4][21], eb[4][6];
+    T Rb[9], tb[3], xib[6], db;
+};
+
+// Main stage: the update's outputs (through io.out), and the reverse pass of
+// everything but the identity messages and the final Exp(xi); the adjoints of
+// the inputs it reaches go through io.add_*, the rest into `o`.
+template <typename T, typename IO>
+PV_HD void pixel_vjp_main(IO& io, const PixCtx<T>& c, MainOut<T>& o) {
     const T lam_R = c.lam_R, beta = c.beta, omb = T(1) - c.beta;
     // ---------------- forward ----------------
     T xi[6];
@@ -447,23 +475,14 @@ PV_HD void pixel_vjp(IO& io, const PixCtx<T>& c) {
     }
     T md = c.lam_Z;
     eb[6] -= c.lam_Z * (d - c.d_prior);
-    T Lk[4][21], ek[4][6];  // damped identity messages
+    T Lk[4][21], ek[4][6];  // damped identity messages (io.identity_forward)
     for (int k = 0; k < 4; ++k) {
         for (int q = 0; q < 21; ++q) Lk[k][q] = T(0);
         for (int q = 0; q < 6; ++q) ek[k][q] = T(0);
         if (!c.has[k]) continue;
-        T nbk[NB_VALS];
-        for (int q = 0; q < NB_VALS; ++q) nbk[q] = io.nb(k, q);
-        T rb[6], W[21], L[21], z[6], iuz, Ln[21], en[6];
-        identity_message(nbk, R, t, lam_R, rb, W, L, z, &iuz, Ln, en);
-        for (int q = 0; q < 6; ++q) {
-            ek[k][q] = omb * en[q] + beta * io.msg(k, 21 + q);
-            eb[q] += ek[k][q];
-        }
-        for (int q = 0; q < 21; ++q) {
-            Lk[k][q] = omb * Ln[q] + beta * io.msg(k, q);
-            Mp[q] += Lk[k][q];
-        }
+        io.identity_forward(k, R, t, Lk[k], ek[k]);
+        for (int q = 0; q < 6; ++q) eb[q] += ek[k][q];
+        for (int q = 0; q < 21; ++q) Mp[q] += Lk[k][q];
     }
     T nl[4], ne[4];
     for (int k = 0; k < 4; ++k) {
@@ -775,108 +794,144 @@ PV_HD void pixel_vjp(IO& io, const PixCtx<T>& c) {
         io.add_nb(k, NB_DJ, -rnb);
     }
     io.add_lamN(lamNb);
-    // identity messages
+    // the damped identity messages enter M_p and eta_b; own old messages (damping)
     for (int k = 0; k < 4; ++k) {
+        for (int q = 0; q < 21; ++q) o.Lb[k][q] = c.has[k] ? Lk[k][q] + Mpb[q] : T(0);
+        for (int q = 0; q < 6; ++q) o.eb[k][q] = c.has[k] ? ek[k][q] + ebb[q] : T(0);
         if (!c.has[k]) continue;
-        T nbk[NB_VALS];
-        for (int q = 0; q < NB_VALS; ++q) nbk[q] = io.nb(k, q);
-        T rb[6], W[21], L[21], z[6], iuz, Ln[21], en[6];
-        identity_message(nbk, R, t, lam_R, rb, W, L, z, &iuz, Ln, en);
-        for (int q = 0; q < 21; ++q) Lk[k][q] += Mpb[q];
-        for (int q = 0; q < 6; ++q) ek[k][q] += ebb[q];
-        for (int q = 0; q < 21; ++q) io.add_msg(k, q, beta * Lk[k][q]);
-        for (int q = 0; q < 6; ++q) io.add_msg(k, 21 + q, beta * ek[k][q]);
-        const T* uj = nbk + NB_U;
-        // y = C^-1 q = eta_new / lam_R; w = lam_R C^-1 eta_new_bar
-        T yv[6], wv[6], eb_[6];
-        for (int q = 0; q < 6; ++q) {
-            yv[q] = en[q] / lam_R;
-            eb_[q] = omb * ek[k][q];
-        }
-        solve_C(L, z, iuz, uj, eb_, wv);
-        for (int q = 0; q < 6; ++q) wv[q] *= lam_R;
-        // C_bar = lam_R^2 C^-1 G C^-1 - w y^T (full matrix)
-        T G[36], X[36], Cb[36];
-        {
-            T Lnb[21];
-            for (int q = 0; q < 21; ++q) Lnb[q] = omb * Lk[k][q];
-            full_from_packed_adjoint(Lnb, G);
-        }
-        for (int cc = 0; cc < 6; ++cc) {  // X = C^-1 G (columns)
-            T col[6], o[6];
-            for (int r = 0; r < 6; ++r) col[r] = G[6 * r + cc];
-            solve_C(L, z, iuz, uj, col, o);
-            for (int r = 0; r < 6; ++r) X[6 * r + cc] = o[r];
-        }
-        for (int r = 0; r < 6; ++r) {  // Cb = lam_R^2 X C^-1 = lam_R^2 (C^-1 X^T)^T
-            T row[6], o[6];
-            for (int cc = 0; cc < 6; ++cc) row[cc] = X[6 * r + cc];
-            solve_C(L, z, iuz, uj, row, o);
-            for (int cc = 0; cc < 6; ++cc) Cb[6 * r + cc] = lam_R * lam_R * o[cc] - wv[r] * yv[cc];
-        }
-        // C = W + lam_R I + u u^T
-        T Wb[21];
-        for (int q = 0; q < 21; ++q) Wb[q] = T(0);
-        add_packed_from_full(Cb, T(1), Wb);
-        T ub[6];
-        for (int r = 0; r < 6; ++r) {
-            T acc = T(0);
-            for (int cc = 0; cc < 6; ++cc) acc += (Cb[6 * r + cc] + Cb[6 * cc + r]) * uj[cc];
-            ub[r] = acc;
-        }
-        // q = g0 - u (u^T rb), g0 = -eta_J - W rb; q_bar = w
-        T urb = T(0), uw = T(0);
-        for (int q = 0; q < 6; ++q) {
-            urb += uj[q] * rb[q];
-            uw += uj[q] * wv[q];
-        }
-        T rbb[6], Ww[6];
-        sym_mv(W, wv, Ww);
-        for (int q = 0; q < 6; ++q) {
-            ub[q] -= wv[q] * urb + rb[q] * uw;
-            rbb[q] = -uj[q] * uw - Ww[q];
-            io.add_nb(k, NB_ME + q, -wv[q]);
-        }
-        add_packed_outer(wv, rb, T(-1), Wb);
-        for (int q = 0; q < 6; ++q) io.add_nb(k, NB_U + q, ub[q]);
-        for (int q = 0; q < 21; ++q) {
-            io.add_nb(k, NB_MP + q, Wb[q]);
-            io.add_nb(k, NB_ML + q, -Wb[q]);
-        }
-        // rb = Log(Exp(xi_j)^-1 Exp(xi_i))
-        T Rj[9], tj[3], Rr[9], tr[3];
-        se3_exp(nbk + NB_XJ, Rj, tj);
-        se3_invmul(Rj, tj, R, t, Rr, tr);
-        T Rrb[9], trb[3];
-        for (int q = 0; q < 9; ++q) Rrb[q] = T(0);
-        for (int q = 0; q < 3; ++q) trb[q] = T(0);
-        log_vjp(Rr, tr, rbb, Rrb, trb);
-        // Rr = Rj^T R, tr = Rj^T (t - tj)
-        T Rjb[9], tjb[3];
-        const T dl[3] = {t[0] - tj[0], t[1] - tj[1], t[2] - tj[2]};
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) {
-                T a1 = T(0), a2 = T(0);
-                for (int m = 0; m < 3; ++m) {
-                    a1 += R[3 * i + m] * Rrb[3 * j + m];   // (R Rr_bar^T)_ij
-                    a2 += Rj[3 * i + m] * Rrb[3 * m + j];  // (Rj Rr_bar)_ij
-                }
-                Rjb[3 * i + j] = a1 + dl[i] * trb[j];
-                Rb[3 * i + j] += a2;
-            }
-        for (int i = 0; i < 3; ++i) {
-            const T v = Rj[3 * i] * trb[0] + Rj[3 * i + 1] * trb[1] + Rj[3 * i + 2] * trb[2];
-            tb[i] += v;
-            tjb[i] = -v;
-        }
-        T xjb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-        exp_vjp(nbk + NB_XJ, Rjb, tjb, xjb);
-        for (int q = 0; q < 6; ++q) io.add_nb(k, NB_XJ + q, xjb[q]);
+        for (int q = 0; q < 21; ++q) io.add_msg(k, q, beta * o.Lb[k][q]);
+        for (int q = 0; q < 6; ++q) io.add_msg(k, 21 + q, beta * o.eb[k][q]);
     }
-    // own pose: Exp(xi) -> (R, t)
+    for (int q = 0; q < 9; ++q) o.Rb[q] = Rb[q];
+    for (int q = 0; q < 3; ++q) o.tb[q] = tb[q];
+    for (int q = 0; q < 6; ++q) o.xib[q] = xib[q];
+    o.db = db;
+}
+
+// Per-direction stage: the reverse pass of the identity message of direction k
+// (Eq. 5 through the Schur complement) at the pixel's pose (R, t), given the
+// adjoints of its damped value (Lbar packed, ebar); adds the adjoints of the
+// neighbour's values through io.add_nb and the pose's to (Rb, tb).
+template <typename T, typename IO>
+PV_HD void identity_vjp(IO& io, const PixCtx<T>& c, int k, const T* R, const T* t, const T* Lbar, const T* ebar,
+                        T* Rb, T* tb) {
+    const T lam_R = c.lam_R, omb = T(1) - c.beta;
+    T nbk[NB_VALS];
+    for (int q = 0; q < NB_VALS; ++q) nbk[q] = io.nb(k, q);
+    T rb[6], W[21], L[21], z[6], iuz, Ln[21], en[6];
+    identity_message(nbk, R, t, lam_R, rb, W, L, z, &iuz, Ln, en);
+    const T* uj = nbk + NB_U;
+    // y = C^-1 q = eta_new / lam_R; w = lam_R C^-1 eta_new_bar
+    T yv[6], wv[6], eb_[6];
+    for (int q = 0; q < 6; ++q) {
+        yv[q] = en[q] / lam_R;
+        eb_[q] = omb * ebar[q];
+    }
+    solve_C(L, z, iuz, uj, eb_, wv);
+    for (int q = 0; q < 6; ++q) wv[q] *= lam_R;
+    // C_bar = lam_R^2 C^-1 G C^-1 - w y^T (full matrix)
+    T G[36], X[36], Cb[36];
+    {
+        T Lnb[21];
+        for (int q = 0; q < 21; ++q) Lnb[q] = omb * Lbar[q];
+        full_from_packed_adjoint(Lnb, G);
+    }
+    for (int cc = 0; cc < 6; ++cc) {  // X = C^-1 G (columns)
+        T col[6], o[6];
+        for (int r = 0; r < 6; ++r) col[r] = G[6 * r + cc];
+        solve_C(L, z, iuz, uj, col, o);
+        for (int r = 0; r < 6; ++r) X[6 * r + cc] = o[r];
+    }
+    for (int r = 0; r < 6; ++r) {  // Cb = lam_R^2 X C^-1 = lam_R^2 (C^-1 X^T)^T
+        T row[6], o[6];
+        for (int cc = 0; cc < 6; ++cc) row[cc] = X[6 * r + cc];
+        solve_C(L, z, iuz, uj, row, o);
+        for (int cc = 0; cc < 6; ++cc) Cb[6 * r + cc] = lam_R * lam_R * o[cc] - wv[r] * yv[cc];
+    }
+    // C = W + lam_R I + u u^T
+    T Wb[21];
+    for (int q = 0; q < 21; ++q) Wb[q] = T(0);
+    add_packed_from_full(Cb, T(1), Wb);
+    T ub[6];
+    for (int r = 0; r < 6; ++r) {
+        T acc = T(0);
+        for (int cc = 0; cc < 6; ++cc) acc += (Cb[6 * r + cc] + Cb[6 * cc + r]) * uj[cc];
+        ub[r] = acc;
+    }
+    // q = g0 - u (u^T rb), g0 = -eta_J - W rb; q_bar = w
+    T urb = T(0), uw = T(0);
+    for (int q = 0; q < 6; ++q) {
+        urb += uj[q] * rb[q];
+        uw += uj[q] * wv[q];
+    }
+    T rbb[6], Ww[6];
+    sym_mv(W, wv, Ww);
+    for (int q = 0; q < 6; ++q) {
+        ub[q] -= wv[q] * urb + rb[q] * uw;
+        rbb[q] = -uj[q] * uw - Ww[q];
+        io.add_nb(k, NB_ME + q, -wv[q]);
+    }
+    add_packed_outer(wv, rb, T(-1), Wb);
+    for (int q = 0; q < 6; ++q) io.add_nb(k, NB_U + q, ub[q]);
+    for (int q = 0; q < 21; ++q) {
+        io.add_nb(k, NB_MP + q, Wb[q]);
+        io.add_nb(k, NB_ML + q, -Wb[q]);
+    }
+    // rb = Log(Exp(xi_j)^-1 Exp(xi_i))
+    T Rj[9], tj[3], Rr[9], tr[3];
+    se3_exp(nbk + NB_XJ, Rj, tj);
+    se3_invmul(Rj, tj, R, t, Rr, tr);
+    T Rrb[9], trb[3];
+    for (int q = 0; q < 9; ++q) Rrb[q] = T(0);
+    for (int q = 0; q < 3; ++q) trb[q] = T(0);
+    log_vjp(Rr, tr, rbb, Rrb, trb);
+    // Rr = Rj^T R, tr = Rj^T (t - tj)
+    T Rjb[9], tjb[3];
+    const T dl[3] = {t[0] - tj[0], t[1] - tj[1], t[2] - tj[2]};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            T a1 = T(0), a2 = T(0);
+            for (int m = 0; m < 3; ++m) {
+                a1 += R[3 * i + m] * Rrb[3 * j + m];   // (R Rr_bar^T)_ij
+                a2 += Rj[3 * i + m] * Rrb[3 * m + j];  // (Rj Rr_bar)_ij
+            }
+            Rjb[3 * i + j] = a1 + dl[i] * trb[j];
+            Rb[3 * i + j] += a2;
+        }
+    for (int i = 0; i < 3; ++i) {
+        const T v = Rj[3 * i] * trb[0] + Rj[3 * i + 1] * trb[1] + Rj[3 * i + 2] * trb[2];
+        tb[i] += v;
+        tjb[i] = -v;
+    }
+    T xjb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    exp_vjp(nbk + NB_XJ, Rjb, tjb, xjb);
+    for (int q = 0; q < 6; ++q) io.add_nb(k, NB_XJ + q, xjb[q]);
+}
+
+// Pose stage: xi_bar from the accumulated (R_bar, t_bar) of Exp(xi), plus the
+// prior's part, and the log-depth's adjoint.
+template <typename T, typename IO>
+PV_HD void pose_vjp(IO& io, const T* xi, const T* Rb, const T* tb, const T* xib_in, T db) {
+    T xib[6];
+    for (int q = 0; q < 6; ++q) xib[q] = xib_in[q];
     exp_vjp(xi, Rb, tb, xib);
     for (int q = 0; q < 6; ++q) io.add_mu(q, xib[q]);
     io.add_mu(6, db);
+}
+
+// The whole reverse pass of one pixel in one thread: the update's outputs
+// (through io.out) and the adjoints of its inputs (through io.add_*) for the
+// output adjoints io.ybar.
+template <typename T, typename IO>
+PV_HD void pixel_vjp(IO& io, const PixCtx<T>& c) {
+    MainOut<T> o;
+    pixel_vjp_main(io, c, o);
+    T xi[6], R[9], t[3];
+    for (int q = 0; q < 6; ++q) xi[q] = io.mu(q);
+    se3_exp(xi, R, t);
+    for (int k = 0; k < 4; ++k)
+        if (c.has[k]) identity_vjp(io, c, k, R, t, o.Lb[k], o.eb[k], o.Rb, o.tb);
+    pose_vjp(io, xi, o.Rb, o.tb, o.xib, o.db);
 }
 
 }  // namespace hw
