@@ -779,7 +779,7 @@ def run_adjoint(args):
     30 sweeps per frame, checkpoints every 5 sweeps. One step = every sequence
     tracks one frame (FP32 state, recording on) and back-propagates the frame's
     loss |xi_est - xi_gt|^2 + mean_px (exp(-mu_6) - 1/z_gt)^2 through its sweeps
-    (FP64 adjoint), giving dL/dsigma_D, dL/dsigma_N, dL/dI_s and dL/dI_t. The same
+    (hand-written adjoint in the state's FP32), giving dL/dsigma_D, dL/dsigma_N, dL/dI_s and dL/dI_t. The same
     frames are also tracked without recording or backward, for the ratio."""
     import multiprocessing as mp
     import synth

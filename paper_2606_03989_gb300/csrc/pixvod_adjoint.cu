@@ -26,8 +26,10 @@ __device__ __forceinline__ T ld(const void* p, size_t i) {
 // writes (its loads then take the read-only path and need not wait for its
 // stores and atomics).
 constexpr int SCR_FWD = 0;   // damped identity messages, slot k at 27 k
-constexpr int SCR_MSG = 108, SCR_RB = 216, SCR_TB = 225, SCR_XIB = 228, SCR_DB = 234;
-constexpr int SCR_PLANES = 236;
+constexpr int SCR_MSG = 108;  // the main stage's outputs, plane SCR_MSG + hw::MO_*
+constexpr int SCR_RB = SCR_MSG + hw::MO_RB, SCR_TB = SCR_MSG + hw::MO_TB, SCR_XIB = SCR_MSG + hw::MO_XIB,
+              SCR_DB = SCR_MSG + hw::MO_DB;
+constexpr int SCR_PLANES = SCR_MSG + hw::MO_PLANES;
 constexpr int SCR_WORDS = SCR_PLANES * TILE_PX;
 
 // I/O of one pixel's reverse pass in the kernel: reads from the state before
@@ -60,12 +62,16 @@ struct KernelIO {
     __device__ T I_s() const { return Is; }
     __device__ T tap(int q) const { return tapv[q]; }
     __device__ T ybar(int q) const { return __ldg(Ao + si + q * TILE_PX) * in_scale; }
-    // the damped identity messages, written to the scratch by k_adjoint_fwd
+    // the damped identity messages, written to the scratch by k_adjoint_fwd,
+    // and the main stage's outputs (another region of the same scratch)
     const T* scr_in;
+    T* scr_out;
+    __device__ T damped(int k, int q) const { return __ldg(scr_in + (SCR_FWD + 27 * k + q) * TILE_PX); }
     __device__ void identity_forward(int k, const T*, const T*, T* L, T* e) const {
-        for (int q = 0; q < 21; ++q) L[q] = __ldg(scr_in + (SCR_FWD + 27 * k + q) * TILE_PX);
-        for (int q = 0; q < 6; ++q) e[q] = __ldg(scr_in + (SCR_FWD + 27 * k + 21 + q) * TILE_PX);
+        for (int q = 0; q < 21; ++q) L[q] = damped(k, q);
+        for (int q = 0; q < 6; ++q) e[q] = damped(k, 21 + q);
     }
+    __device__ void main_out(int p, T v) const { scr_out[(SCR_MSG + p) * TILE_PX] = v; }
     __device__ void out(int q, T y, T scale) {
         const T ref = __ldg(Sout + si + q * TILE_PX);
         const T den = v_abs(ref) > scale ? v_abs(ref) : scale;
@@ -120,6 +126,7 @@ __device__ bool pixel_context(const AdjArgs& A, int tile, int lane, hw::PixCtx<T
     io.si = (size_t)tile * TILE_WORDS + lane;
     io.mm = T(0);
     io.scr_in = nullptr;
+    io.scr_out = nullptr;
     io.dIs = io.lamD = io.isD = io.lamN = 0.0;
     io.in_scale = T(1);
     io.out_scale = 1.0;
@@ -236,16 +243,8 @@ __global__ void __launch_bounds__(TILE_PX, sizeof(T) == 4 ? PV_ADJ_MAIN_BLOCKS :
         }
         T* sp = scr + (size_t)tile * SCR_WORDS + lane;
         io.scr_in = sp;
-        hw::MainOut<T> o;
-        hw::pixel_vjp_main(io, c, o);
-        for (int k = 0; k < 4; ++k) {
-            for (int q = 0; q < 21; ++q) sp[(SCR_MSG + 27 * k + q) * TILE_PX] = o.Lb[k][q];
-            for (int q = 0; q < 6; ++q) sp[(SCR_MSG + 27 * k + 21 + q) * TILE_PX] = o.eb[k][q];
-        }
-        for (int q = 0; q < 9; ++q) sp[(SCR_RB + q) * TILE_PX] = o.Rb[q];
-        for (int q = 0; q < 3; ++q) sp[(SCR_TB + q) * TILE_PX] = o.tb[q];
-        for (int q = 0; q < 6; ++q) sp[(SCR_XIB + q) * TILE_PX] = o.xib[q];
-        sp[SCR_DB * TILE_PX] = o.db;
+        io.scr_out = sp;
+        hw::pixel_vjp_main(io, c);
         atomic_max_nonneg(A.mismatch, double(io.mm));
         A.dI_s[(size_t)v * W + u] += io.dIs;
         atomicAdd(&red[0], io.lamD);

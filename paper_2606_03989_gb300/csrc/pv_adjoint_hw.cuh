@@ -289,6 +289,10 @@ constexpr int N_OUT = 151; // output planes, in state order
 //   T ybar(q)                       adjoint of output plane q (state order)
 //   void identity_forward(k, R, t, L, e)  the damped identity message of
 //                                   direction k (damped_identity, or precomputed)
+//   T damped(k, q)                  value q (Lambda packed, eta) of that message
+//                                   again, for a direction with a neighbour
+//   void main_out(p, v)             what the main stage hands on (plane p, MO_*)
+//   T main_in(p)                    that value back (pixel_vjp only)
 //   void out(q, y, scale)           recomputed output plane q and the magnitude
 //                                   of the terms it is formed from (>= 1, >= |y|)
 //   void add_mu/add_msg/add_nm/add_nb/add_Is/add_tap(..., v), add_lamD/add_isD/
@@ -445,20 +449,20 @@ PV_HD void damped_identity(IO& io, const PixCtx<T>& c, int k, const T* R, const 
 }
 
 // What the main stage of the reverse pass hands to the per-direction and pose
-// stages: the adjoints of the four damped identity messages (Lambda packed, eta),
-// of the pixel's rotation and translation (R, t = Exp(xi)), of xi through the
-// prior, and of the log-depth.
-template <typename T>
-struct MainOut {
-    T Lb[4][21], eb[4][6];
-    T Rb[9], tb[3], xib[6], db;
-};
+// stages (planes of io.main_out): the adjoints of the damped identity message of
+// each direction with a neighbour (27 k + q: Lambda packed, eta), of the pixel's
+// rotation and translation (R, t = Exp(xi)), of xi through the prior, and of the
+// log-depth.
+constexpr int MO_MSG = 0, MO_RB = 108, MO_TB = 117, MO_XIB = 120, MO_DB = 126;
+constexpr int MO_PLANES = 127;
 
 // Main stage: the update's outputs (through io.out), and the reverse pass of
 // everything but the identity messages and the final Exp(xi); the adjoints of
-// the inputs it reaches go through io.add_*, the rest into `o`.
+// the inputs it reaches go through io.add_*, the rest through io.main_out. The
+// damped identity messages are not kept: they are read again (io.damped) where
+// the output check and the reverse pass need them.
 template <typename T, typename IO>
-PV_HD void pixel_vjp_main(IO& io, const PixCtx<T>& c, MainOut<T>& o) {
+PV_HD void pixel_vjp_main(IO& io, const PixCtx<T>& c) {
     const T lam_R = c.lam_R, beta = c.beta, omb = T(1) - c.beta;
     // ---------------- forward ----------------
     T xi[6];
@@ -475,14 +479,12 @@ PV_HD void pixel_vjp_main(IO& io, const PixCtx<T>& c, MainOut<T>& o) {
     }
     T md = c.lam_Z;
     eb[6] -= c.lam_Z * (d - c.d_prior);
-    T Lk[4][21], ek[4][6];  // damped identity messages (io.identity_forward)
     for (int k = 0; k < 4; ++k) {
-        for (int q = 0; q < 21; ++q) Lk[k][q] = T(0);
-        for (int q = 0; q < 6; ++q) ek[k][q] = T(0);
         if (!c.has[k]) continue;
-        io.identity_forward(k, R, t, Lk[k], ek[k]);
-        for (int q = 0; q < 6; ++q) eb[q] += ek[k][q];
-        for (int q = 0; q < 21; ++q) Mp[q] += Lk[k][q];
+        T L[21], e[6];  // the damped identity message
+        io.identity_forward(k, R, t, L, e);
+        for (int q = 0; q < 6; ++q) eb[q] += e[q];
+        for (int q = 0; q < 21; ++q) Mp[q] += L[q];
     }
     T nl[4], ne[4];
     for (int k = 0; k < 4; ++k) {
@@ -551,12 +553,15 @@ PV_HD void pixel_vjp_main(IO& io, const PixCtx<T>& c, MainOut<T>& o) {
     for (int q = 0; q < 6; ++q) out_plain(28 + q, sb * J[q]);
     out_plain(34, md + v_div(alpha * J[6] * J[6], es));
     for (int k = 0; k < 4; ++k) {
-        for (int q = 0; q < 21; ++q) out_plain(35 + 27 * k + q, Lk[k][q]);
+        T L[21], el[6];
+        for (int q = 0; q < 21; ++q) L[q] = c.has[k] ? io.damped(k, q) : T(0);
+        for (int q = 0; q < 6; ++q) el[q] = c.has[k] ? io.damped(k, 21 + q) : T(0);
+        for (int q = 0; q < 21; ++q) out_plain(35 + 27 * k + q, L[q]);
         for (int r = 0; r < 6; ++r) {
-            T e = ek[k][r], m = v_abs(ek[k][r]);
+            T e = el[r], m = v_abs(el[r]);
             for (int cc = 0; cc < 6; ++cc) {
-                e -= Lk[k][pidx(r, cc)] * tau[cc];
-                m += v_abs(Lk[k][pidx(r, cc)] * tau[cc]);
+                e -= L[pidx(r, cc)] * tau[cc];
+                m += v_abs(L[pidx(r, cc)] * tau[cc]);
             }
             io.out(35 + 27 * k + 21 + r, e, m > v_abs(e) ? (m > T(1) ? m : T(1)) : (v_abs(e) > T(1) ? v_abs(e) : T(1)));
         }
@@ -575,18 +580,16 @@ PV_HD void pixel_vjp_main(IO& io, const PixCtx<T>& c, MainOut<T>& o) {
     }
     for (int q = 0; q < 9; ++q) Rb[q] = T(0);
     for (int q = 0; q < 3; ++q) tb[q] = T(0);
-    // projected messages eta' = eta - Lambda tau, and the normal ones; Lk, ek
-    // now hold the adjoints of the damped messages
+    // projected messages eta' = eta - Lambda tau (the adjoints of the damped
+    // messages themselves are formed at the end), and the normal ones
     T nlb[4], neb[4];
     for (int k = 0; k < 4; ++k) {
-        T eyb[6];
+        T eyb[6], L[21];
         for (int r = 0; r < 6; ++r) eyb[r] = io.ybar(35 + 27 * k + 21 + r);
+        for (int q = 0; q < 21; ++q) L[q] = c.has[k] ? io.damped(k, q) : T(0);
         T tmp[6];
-        sym_mv(Lk[k], eyb, tmp);
+        sym_mv(L, eyb, tmp);
         for (int q = 0; q < 6; ++q) taub[q] -= tmp[q];
-        for (int q = 0; q < 21; ++q) Lk[k][q] = io.ybar(35 + 27 * k + q);
-        for (int r = 0; r < 6; ++r) ek[k][r] = eyb[r];
-        add_packed_outer(eyb, tau, T(-1), Lk[k]);
         const T nyb = io.ybar(143 + 2 * k), eyn = io.ybar(144 + 2 * k);
         nlb[k] = nyb - eyn * tau[6];
         neb[k] = eyn;
@@ -794,18 +797,30 @@ PV_HD void pixel_vjp_main(IO& io, const PixCtx<T>& c, MainOut<T>& o) {
         io.add_nb(k, NB_DJ, -rnb);
     }
     io.add_lamN(lamNb);
-    // the damped identity messages enter M_p and eta_b; own old messages (damping)
+    // the damped identity messages: their adjoints from the projected outputs
+    // (Lambda' = Lambda, eta' = eta - Lambda tau) and from M_p and eta_b; own
+    // old messages (damping)
     for (int k = 0; k < 4; ++k) {
-        for (int q = 0; q < 21; ++q) o.Lb[k][q] = c.has[k] ? Lk[k][q] + Mpb[q] : T(0);
-        for (int q = 0; q < 6; ++q) o.eb[k][q] = c.has[k] ? ek[k][q] + ebb[q] : T(0);
         if (!c.has[k]) continue;
-        for (int q = 0; q < 21; ++q) io.add_msg(k, q, beta * o.Lb[k][q]);
-        for (int q = 0; q < 6; ++q) io.add_msg(k, 21 + q, beta * o.eb[k][q]);
+        T Lb[21], eyb[6];
+        for (int q = 0; q < 21; ++q) Lb[q] = io.ybar(35 + 27 * k + q);
+        for (int r = 0; r < 6; ++r) eyb[r] = io.ybar(35 + 27 * k + 21 + r);
+        add_packed_outer(eyb, tau, T(-1), Lb);
+        for (int q = 0; q < 21; ++q) {
+            const T v = Lb[q] + Mpb[q];
+            io.main_out(MO_MSG + 27 * k + q, v);
+            io.add_msg(k, q, beta * v);
+        }
+        for (int q = 0; q < 6; ++q) {
+            const T v = eyb[q] + ebb[q];
+            io.main_out(MO_MSG + 27 * k + 21 + q, v);
+            io.add_msg(k, 21 + q, beta * v);
+        }
     }
-    for (int q = 0; q < 9; ++q) o.Rb[q] = Rb[q];
-    for (int q = 0; q < 3; ++q) o.tb[q] = tb[q];
-    for (int q = 0; q < 6; ++q) o.xib[q] = xib[q];
-    o.db = db;
+    for (int q = 0; q < 9; ++q) io.main_out(MO_RB + q, Rb[q]);
+    for (int q = 0; q < 3; ++q) io.main_out(MO_TB + q, tb[q]);
+    for (int q = 0; q < 6; ++q) io.main_out(MO_XIB + q, xib[q]);
+    io.main_out(MO_DB, db);
 }
 
 // Per-direction stage: the reverse pass of the identity message of direction k
@@ -924,14 +939,21 @@ PV_HD void pose_vjp(IO& io, const T* xi, const T* Rb, const T* tb, const T* xib_
 // output adjoints io.ybar.
 template <typename T, typename IO>
 PV_HD void pixel_vjp(IO& io, const PixCtx<T>& c) {
-    MainOut<T> o;
-    pixel_vjp_main(io, c, o);
-    T xi[6], R[9], t[3];
+    pixel_vjp_main(io, c);
+    T xi[6], R[9], t[3], Rb[9], tb[3], xib[6];
     for (int q = 0; q < 6; ++q) xi[q] = io.mu(q);
     se3_exp(xi, R, t);
-    for (int k = 0; k < 4; ++k)
-        if (c.has[k]) identity_vjp(io, c, k, R, t, o.Lb[k], o.eb[k], o.Rb, o.tb);
-    pose_vjp(io, xi, o.Rb, o.tb, o.xib, o.db);
+    for (int q = 0; q < 9; ++q) Rb[q] = io.main_in(MO_RB + q);
+    for (int q = 0; q < 3; ++q) tb[q] = io.main_in(MO_TB + q);
+    for (int q = 0; q < 6; ++q) xib[q] = io.main_in(MO_XIB + q);
+    for (int k = 0; k < 4; ++k) {
+        if (!c.has[k]) continue;
+        T Lb[21], eb[6];
+        for (int q = 0; q < 21; ++q) Lb[q] = io.main_in(MO_MSG + 27 * k + q);
+        for (int q = 0; q < 6; ++q) eb[q] = io.main_in(MO_MSG + 27 * k + 21 + q);
+        identity_vjp(io, c, k, R, t, Lb, eb, Rb, tb);
+    }
+    pose_vjp(io, xi, Rb, tb, xib, io.main_in(MO_DB));
 }
 
 }  // namespace hw
