@@ -611,11 +611,10 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
             } else {
                 // rescale by a power of two: max |adj_out|, the pass, the new exponent
                 if ((s = cuda_status(cudaMemsetAsync(scale + 1, 0, sizeof(double), st))) != PIXVOD_OK) return s;
-                h->launches += 3;
+                h->launches += 2 + pv::ADJOINT_HW_LAUNCHES;  // absmax, the pass, the exponent
                 if ((s = cuda_status(pv::launch_adjoint_absmax(adj[a], adj_elems, adj64 ? 1 : 0, scale, st))) !=
                     PIXVOD_OK)
                     return s;
-                h->launches += 3;
                 if ((s = cuda_status(pv::launch_adjoint_hw(A, n_tiles, rw + R.off_scr, st))) != PIXVOD_OK) return s;
                 if ((s = cuda_status(pv::launch_adjoint_exponent(scale, st))) != PIXVOD_OK) return s;
             }

@@ -1,7 +1,8 @@
 // Adjoint kernels of the sweep, compiled on their own: their launchers are
 // called from pixvod.cu. Two reverse passes of one sweep exist:
-//  - k_adjoint_hw<T>: the hand-written reverse pass (pv_adjoint_hw.cuh) in the
-//    state's precision, one thread per pixel, no tape; the product path;
+//  - the hand-written reverse pass (pv_adjoint_hw.cuh) in the state's
+//    precision, no tape, in stages (k_adjoint_fwd, _main, _dir, _check, _pose);
+//    the product path;
 //  - k_adjoint_sweep: a reverse-mode tape of the same update in FP64
 //    (pv_adjoint.cuh), kept to cross-check the hand-written pass.
 #include "pv_adjoint.cuh"
@@ -18,18 +19,29 @@ __device__ __forceinline__ T ld(const void* p, size_t i) {
 
 // Scratch between the stages of the hand-written pass, tile-major like the
 // state (plane p of a tile's pixel `lane` at tile * SCR_WORDS + p * TILE_PX +
-// lane): the adjoints of the four damped identity messages (slot k at 27 k:
-// Lambda packed, eta), of R (9), t (3), xi through the prior (6) and of the
-// log-depth (1).
-// Two regions: the damped messages the forward stage computes (read by the main
-// stage), then what the main stage hands on, so that no kernel reads a buffer it
-// writes (its loads then take the read-only path and need not wait for its
-// stores and atomics).
-constexpr int SCR_FWD = 0;   // damped identity messages, slot k at 27 k
-constexpr int SCR_MSG = 108;  // the main stage's outputs, plane SCR_MSG + hw::MO_*
-constexpr int SCR_RB = SCR_MSG + hw::MO_RB, SCR_TB = SCR_MSG + hw::MO_TB, SCR_XIB = SCR_MSG + hw::MO_XIB,
-              SCR_DB = SCR_MSG + hw::MO_DB;
-constexpr int SCR_PLANES = SCR_MSG + hw::MO_PLANES;
+// lane). Regions:
+//   SCR_FWD   the damped identity messages (direction k at 27 k: Lambda
+//             packed, eta), from k_adjoint_fwd, read by k_adjoint_dir;
+//   SCR_SUM   their sums over the directions (Lambda 21, eta 6) and the sum of
+//             Lambda_k ybar(eta_k') (6), from k_adjoint_fwd, read by the main
+//             stage;
+//   SCR_MAIN  what the main stage hands on (hw::MO_*); k_adjoint_dir adds its
+//             R and t adjoints to the MO_RB and MO_TB planes;
+//   SCR_CHK   the main stage's recomputed outputs (all but the identity
+//             messages': outputs 0-34 and 143-150, chk_plane) and
+//   SCR_CHK_S the scales of the normal messages' eta (formed by cancelling
+//             terms), read by k_adjoint_check.
+// No kernel loads a plane that it writes (its loads take the read-only path and
+// need not wait for its stores and atomics).
+constexpr int SCR_FWD = 0;
+constexpr int SCR_SUM = SCR_FWD + 108;
+constexpr int SCR_MAIN = SCR_SUM + 33;
+constexpr int SCR_CHK = SCR_MAIN + hw::MO_PLANES;
+constexpr int SCR_CHK_S = SCR_CHK + 43;
+constexpr int SCR_PLANES = SCR_CHK_S + 4;
+
+// plane of output q (not an identity message's) in SCR_CHK
+__host__ __device__ constexpr int chk_plane(int q) { return q < 35 ? q : q - 108; }
 constexpr int SCR_WORDS = SCR_PLANES * TILE_PX;
 
 // I/O of one pixel's reverse pass in the kernel: reads from the state before
@@ -39,7 +51,6 @@ constexpr int SCR_WORDS = SCR_PLANES * TILE_PX;
 template <typename T>
 struct KernelIO {
     const T* Sin;    // S_{s-1}
-    const T* Sout;   // S_s
     const T* Ao;     // adjoint of S_s
     T* Ai;           // adjoint of S_{s-1}
     double* dI_t;
@@ -49,12 +60,10 @@ struct KernelIO {
     T Is, tapv[12];
     T in_scale;        // 2^-e: adj_out is read in units of 2^(E + e)
     double out_scale;  // 2^(E + e): the FP64 gradients' factor
-    T mm;              // largest relative difference of the recomputed update (in T: FP64 is slow here)
     double dIs, lamD, isD, lamN;
 
-    // the previous state, the next state, the output adjoint and the forward
-    // stage's scratch are read-only while a stage runs: loads take the
-    // non-coherent path
+    // the previous state, the output adjoint and the forward stage's scratch
+    // are read-only while a stage runs: loads take the non-coherent path
     __device__ T mu(int q) const { return __ldg(Sin + si + q * TILE_PX); }
     __device__ T msg(int k, int q) const { return __ldg(Sin + si + (PL_ID + ID_STRIDE * k + q) * TILE_PX); }
     __device__ T nm(int q) const { return __ldg(Sin + si + (PL_NM + q) * TILE_PX); }
@@ -62,21 +71,27 @@ struct KernelIO {
     __device__ T I_s() const { return Is; }
     __device__ T tap(int q) const { return tapv[q]; }
     __device__ T ybar(int q) const { return __ldg(Ao + si + q * TILE_PX) * in_scale; }
-    // the damped identity messages, written to the scratch by k_adjoint_fwd,
-    // and the main stage's outputs (another region of the same scratch)
+    // the stages' scratch (scr_in, scr_out: the pixel's planes)
     const T* scr_in;
     T* scr_out;
-    __device__ T damped(int k, int q) const { return __ldg(scr_in + (SCR_FWD + 27 * k + q) * TILE_PX); }
-    __device__ void identity_forward(int k, const T*, const T*, T* L, T* e) const {
-        for (int q = 0; q < 21; ++q) L[q] = damped(k, q);
-        for (int q = 0; q < 6; ++q) e[q] = damped(k, 21 + q);
+    __device__ void identity_sums(const T*, const T*, T* L, T* e) const {
+        for (int q = 0; q < 21; ++q) L[q] = __ldg(scr_in + (SCR_SUM + q) * TILE_PX);
+        for (int q = 0; q < 6; ++q) e[q] = __ldg(scr_in + (SCR_SUM + 21 + q) * TILE_PX);
     }
-    __device__ void main_out(int p, T v) const { scr_out[(SCR_MSG + p) * TILE_PX] = v; }
-    __device__ void out(int q, T y, T scale) {
-        const T ref = __ldg(Sout + si + q * TILE_PX);
-        const T den = v_abs(ref) > scale ? v_abs(ref) : scale;
-        const T e = v_abs(y - ref) / den;
-        mm = e > mm ? e : mm;
+    __device__ void identity_eta_adj(T* w) const {
+        for (int q = 0; q < 6; ++q) w[q] = __ldg(scr_in + (SCR_SUM + 27 + q) * TILE_PX);
+    }
+    __device__ T damped(int k, int q) const { return __ldg(scr_in + (SCR_FWD + 27 * k + q) * TILE_PX); }
+    __device__ void main_out(int p, T v) const { scr_out[(SCR_MAIN + p) * TILE_PX] = v; }
+    __device__ T main_in(int p) const { return __ldg(scr_in + (SCR_MAIN + p) * TILE_PX); }
+    // the recomputed update goes to the scratch and k_adjoint_check compares it
+    // with the sweep kernel's (the comparison's loads would otherwise stall the
+    // stage's chain)
+    // (the main stage's outputs only: the check forms the identity messages'
+    // itself)
+    __device__ void out(int q, T y, T scale) const {
+        scr_out[(SCR_CHK + chk_plane(q)) * TILE_PX] = y;
+        if (q >= 144 && (q & 1) == 0) scr_out[(SCR_CHK_S + (q - 144) / 2) * TILE_PX] = scale;
     }
     __device__ void add_mu(int q, T v) { atomicAdd(Ai + si + q * TILE_PX, v); }
     __device__ void add_msg(int k, int q, T v) { atomicAdd(Ai + si + (PL_ID + ID_STRIDE * k + q) * TILE_PX, v); }
@@ -117,14 +132,12 @@ __device__ bool pixel_context(const AdjArgs& A, int tile, int lane, hw::PixCtx<T
     *v_out = v;
     if (u >= W || v >= H) return false;
     io.Sin = static_cast<const T*>(A.state_in);
-    io.Sout = static_cast<const T*>(A.state_out);
     io.Ao = static_cast<const T*>(A.adj_out);
     io.Ai = static_cast<T*>(A.adj_in);
     io.dI_t = A.dI_t;
     io.W = W;
     io.H = H;
     io.si = (size_t)tile * TILE_WORDS + lane;
-    io.mm = T(0);
     io.scr_in = nullptr;
     io.scr_out = nullptr;
     io.dIs = io.lamD = io.isD = io.lamN = 0.0;
@@ -164,12 +177,67 @@ __device__ bool pixel_context(const AdjArgs& A, int tile, int lane, hw::PixCtx<T
     return true;
 }
 
-// Main stage of the hand-written adjoint of one sweep (block = one state tile of
-// 32 x 4 pixels, thread = one pixel): recomputes the pixel's update, compares it
-// with the sweep kernel's result, runs the reverse pass of everything but the
-// identity messages and the pose's Exp, adds the adjoints it reaches (own normal
-// and old messages, the normal-factor values read from neighbours, dI_s, dI_t,
-// factor weights) and leaves the rest in the scratch.
+// The adjoint state is rescaled by a power of two before every pass: the
+// unrolled derivative can grow by many orders of magnitude over the sweeps,
+// beyond the float range, while the pass is linear in its input.
+template <typename T>
+__device__ void set_scales(const AdjArgs& A, KernelIO<T>& io) {
+    const double mx = A.scale[1];
+    const int e = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) : 0;
+    io.in_scale = T(ldexp(1.0, -e));
+    io.out_scale = ldexp(1.0, (int)A.scale[0] + e);
+}
+
+// Forward per-direction stage (first): block = one row of 32 pixels of a state
+// tile (grid: tiles x TILE_H), four threads per pixel, one per direction
+// (thread = 4 x column + k). Each recomputes the damped identity message of its
+// direction into SCR_FWD and its Lambda_k ybar(eta_k'); the pixel's four
+// threads, adjacent lanes of one warp, sum both over the directions by shuffles
+// and the first of them writes the sums to SCR_SUM.
+template <typename T>
+__global__ void __launch_bounds__(TILE_PX) k_adjoint_fwd(const AdjArgs A, T* __restrict__ scr) {
+    const int tile = blockIdx.x, k = threadIdx.x & 3;
+    const int lane = blockIdx.y * TILE_W + (threadIdx.x >> 2);
+    KernelIO<T> io;
+    hw::PixCtx<T> c;
+    int u, v;
+    const bool inside = pixel_context(A, tile, lane, c, io, &u, &v);
+    T* sp = scr + (size_t)tile * SCR_WORDS + lane;
+    T L[21], e[6], w[6];
+    for (int q = 0; q < 21; ++q) L[q] = T(0);
+    for (int q = 0; q < 6; ++q) e[q] = w[q] = T(0);
+    if (inside && c.has[k]) {
+        set_scales(A, io);
+        T xi[6], R[9], t[3];
+        for (int q = 0; q < 6; ++q) xi[q] = io.mu(q);
+        se3_exp(xi, R, t);
+        hw::damped_identity(io, c, k, R, t, L, e);
+        hw::identity_w(io, k, L, w);
+        for (int q = 0; q < 21; ++q) sp[(SCR_FWD + 27 * k + q) * TILE_PX] = L[q];
+        for (int q = 0; q < 6; ++q) sp[(SCR_FWD + 27 * k + 21 + q) * TILE_PX] = e[q];
+    }
+    for (int o = 1; o < 4; o <<= 1) {
+        for (int q = 0; q < 21; ++q) L[q] += __shfl_xor_sync(0xffffffffu, L[q], o);
+        for (int q = 0; q < 6; ++q) {
+            e[q] += __shfl_xor_sync(0xffffffffu, e[q], o);
+            w[q] += __shfl_xor_sync(0xffffffffu, w[q], o);
+        }
+    }
+    if (inside && k == 0) {
+        for (int q = 0; q < 21; ++q) sp[(SCR_SUM + q) * TILE_PX] = L[q];
+        for (int q = 0; q < 6; ++q) {
+            sp[(SCR_SUM + 21 + q) * TILE_PX] = e[q];
+            sp[(SCR_SUM + 27 + q) * TILE_PX] = w[q];
+        }
+    }
+}
+
+// Main stage (block = one state tile of 32 x 4 pixels, thread = one pixel):
+// recomputes the pixel's update from the summed damped messages, writes the
+// outputs but the identity messages' for the check, runs the reverse pass of
+// everything but the identity messages and the pose's Exp, adds the adjoints it
+// reaches (own normal messages, the normal-factor values read from neighbours,
+// dI_s, dI_t, factor weights) and leaves the rest in the scratch.
 // FP32 runs 4 blocks per SM at 128 registers: the spills that brings cost less
 // than the occupancy gained (14.5 ms against 17.0 ms at 2 blocks for 30 reverse
 // sweeps at 320 x 240). FP64 keeps every register it asks for.
@@ -188,15 +256,7 @@ __global__ void __launch_bounds__(TILE_PX, sizeof(T) == 4 ? PV_ADJ_MAIN_BLOCKS :
     int u, v;
     if (pixel_context(A, tile, lane, c, io, &u, &v)) {
         const int W = g.W, H = g.H;
-        // the adjoint state is rescaled by a power of two before every pass: the
-        // unrolled derivative can grow by many orders of magnitude over the sweeps,
-        // beyond the float range, while the pass is linear in its input
-        {
-            const double mx = A.scale[1];
-            const int e = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) : 0;
-            io.in_scale = T(ldexp(1.0, -e));
-            io.out_scale = ldexp(1.0, (int)A.scale[0] + e);
-        }
+        set_scales(A, io);
         const size_t ii = (size_t)v * g.pitch + u;
         io.Is = ld<T>(A.I_s, ii);
         // the bilinear cell of the warp at the current mean, with the sweep
@@ -245,7 +305,6 @@ __global__ void __launch_bounds__(TILE_PX, sizeof(T) == 4 ? PV_ADJ_MAIN_BLOCKS :
         io.scr_in = sp;
         io.scr_out = sp;
         hw::pixel_vjp_main(io, c);
-        atomic_max_nonneg(A.mismatch, double(io.mm));
         A.dI_s[(size_t)v * W + u] += io.dIs;
         atomicAdd(&red[0], io.lamD);
         atomicAdd(&red[1], io.isD);
@@ -255,30 +314,11 @@ __global__ void __launch_bounds__(TILE_PX, sizeof(T) == 4 ? PV_ADJ_MAIN_BLOCKS :
     if (lane < 3 && red[lane] != 0.0) atomicAdd(A.dparam + lane, red[lane]);
 }
 
-// Forward per-direction stage (before the main stage): one thread per pixel and
-// direction (block = one state tile, grid.y = the direction) recomputes the
-// damped identity message of that direction into the scratch, so that the main
-// stage does not compute the four in sequence.
-template <typename T>
-__global__ void __launch_bounds__(TILE_PX) k_adjoint_fwd(const AdjArgs A, T* __restrict__ scr) {
-    const int tile = blockIdx.x, lane = threadIdx.x, k = blockIdx.y;
-    KernelIO<T> io;
-    hw::PixCtx<T> c;
-    int u, v;
-    if (!pixel_context(A, tile, lane, c, io, &u, &v) || !c.has[k]) return;
-    T* sp = scr + (size_t)tile * SCR_WORDS + lane;
-    T xi[6], R[9], t[3], L[21], e[6];
-    for (int q = 0; q < 6; ++q) xi[q] = io.mu(q);
-    se3_exp(xi, R, t);
-    hw::damped_identity(io, c, k, R, t, L, e);
-    for (int q = 0; q < 21; ++q) sp[(SCR_FWD + 27 * k + q) * TILE_PX] = L[q];
-    for (int q = 0; q < 6; ++q) sp[(SCR_FWD + 27 * k + 21 + q) * TILE_PX] = e[q];
-}
-
 // Per-direction stage: one thread per pixel and direction (block = one state
-// tile, grid.y = the direction): the reverse pass of that identity message,
-// scattering the neighbour's adjoints and adding the pose's (R, t) adjoints to
-// the scratch.
+// tile, grid.y = the direction): the adjoint of that damped identity message,
+// the damping's adjoint into the pixel's old message, the reverse pass of the
+// message (scattering the neighbour's adjoints), and the pose's (R, t) adjoints
+// added to the scratch.
 template <typename T>
 __global__ void __launch_bounds__(TILE_PX) k_adjoint_dir(const AdjArgs A, T* __restrict__ scr) {
     const int tile = blockIdx.x, lane = threadIdx.x, k = blockIdx.y;
@@ -286,20 +326,153 @@ __global__ void __launch_bounds__(TILE_PX) k_adjoint_dir(const AdjArgs A, T* __r
     hw::PixCtx<T> c;
     int u, v;
     if (!pixel_context(A, tile, lane, c, io, &u, &v) || !c.has[k]) return;
+    set_scales(A, io);
     T* sp = scr + (size_t)tile * SCR_WORDS + lane;
-    T xi[6], R[9], t[3], Lb[21], eb[6], Rb[9], tb[3];
+    io.scr_in = sp;
+    io.scr_out = sp;
+    T Lb[21], eb[6];
+    {
+        T tau[7], Mpb[21], ebb[6];
+        for (int q = 0; q < 7; ++q) tau[q] = io.main_in(hw::MO_TAU + q);
+        for (int q = 0; q < 21; ++q) Mpb[q] = io.main_in(hw::MO_MPB + q);
+        for (int q = 0; q < 6; ++q) ebb[q] = io.main_in(hw::MO_EBB + q);
+        hw::identity_msg_adjoint(io, c, k, tau, Mpb, ebb, Lb, eb);
+    }
+    T xi[6], R[9], t[3], Rb[9], tb[3];
     for (int q = 0; q < 6; ++q) xi[q] = io.mu(q);
     se3_exp(xi, R, t);
-    for (int q = 0; q < 21; ++q) Lb[q] = sp[(SCR_MSG + 27 * k + q) * TILE_PX];
-    for (int q = 0; q < 6; ++q) eb[q] = sp[(SCR_MSG + 27 * k + 21 + q) * TILE_PX];
     for (int q = 0; q < 9; ++q) Rb[q] = T(0);
     for (int q = 0; q < 3; ++q) tb[q] = T(0);
     hw::identity_vjp(io, c, k, R, t, Lb, eb, Rb, tb);
-    for (int q = 0; q < 9; ++q) atomicAdd(sp + (SCR_RB + q) * TILE_PX, Rb[q]);
-    for (int q = 0; q < 3; ++q) atomicAdd(sp + (SCR_TB + q) * TILE_PX, tb[q]);
+    for (int q = 0; q < 9; ++q) atomicAdd(sp + (SCR_MAIN + hw::MO_RB + q) * TILE_PX, Rb[q]);
+    for (int q = 0; q < 3; ++q) atomicAdd(sp + (SCR_MAIN + hw::MO_TB + q) * TILE_PX, tb[q]);
 }
 
-// Pose stage: the pixel's xi adjoint from the (R, t) adjoints of its Exp.
+// Recompute check (after the main stage): block = one state tile, in five
+// groups of threads with 16-byte loads (NV lanes per thread): group 0 checks
+// the outputs the main stage wrote (SCR_CHK: the mean, M_p, u, s and the normal
+// messages), group 1 + k the damped identity message of direction k, formed
+// here from SCR_FWD and tau as the update forms it (Lambda' = Lambda, eta' =
+// eta - Lambda tau, zero without a neighbour). The outputs of a group are known
+// at compile time, so each thread's loads are issued together. Each output is
+// compared with the sweep kernel's relative to max(|stored|, the magnitude of
+// the terms it is formed from); the largest difference goes to A.mismatch (one
+// atomic per block).
+// (divides only when the maximum grows: |y - r| > mm den decides it; a NaN
+// difference never does)
+template <typename T>
+__device__ __forceinline__ void check_value(T yq, T s, T rq, T& mm) {
+    const T den = v_abs(rq) > s ? v_abs(rq) : s;
+    const T d = v_abs(yq - rq);
+    if (d > mm * den) {
+        const T e = d / den;
+        mm = e > mm ? e : mm;
+    }
+}
+
+__device__ __forceinline__ void ld16(const float* p, float* o) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = x.x;
+    o[1] = x.y;
+    o[2] = x.z;
+    o[3] = x.w;
+}
+__device__ __forceinline__ void ld16(const double* p, double* o) {
+    const double2 x = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = x.x;
+    o[1] = x.y;
+}
+
+// one output of the main stage: recomputed values y, stored ref (NV lanes)
+template <typename T, int NV>
+__device__ __forceinline__ void check_main_output(const T* sp, const T* ref, int q, int nval, T& mm) {
+    T y[NV], r[NV], sc[NV];
+    ld16(sp + (SCR_CHK + chk_plane(q)) * TILE_PX, y);
+    ld16(ref + q * TILE_PX, r);
+    if (q >= 144 && (q & 1) == 0)
+        ld16(sp + (SCR_CHK_S + (q - 144) / 2) * TILE_PX, sc);
+    else
+        for (int j = 0; j < NV; ++j) sc[j] = v_abs(y[j]) > T(1) ? v_abs(y[j]) : T(1);
+    for (int j = 0; j < NV; ++j)
+        if (j < nval) check_value(y[j], sc[j], r[j], mm);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(5 * TILE_PX / (16 / sizeof(T))) k_adjoint_check(const AdjArgs A,
+                                                                                   const T* __restrict__ scr) {
+    constexpr int NV = 16 / sizeof(T);  // lanes per thread
+    constexpr int TPR = TILE_PX / NV;   // threads per group
+    const Geometry<double>& g = A.g;
+    const int tile = blockIdx.x, grp = threadIdx.x / TPR, lane0 = (threadIdx.x % TPR) * NV;
+    const int u0 = (tile % g.tiles_x) * TILE_W + lane0 % TILE_W;  // NV pixels u0.. of one image row
+    const int v = (tile / g.tiles_x) * TILE_H + lane0 / TILE_W;
+    const int nval = (v < g.H) ? min(NV, g.W - u0) : 0;  // lanes inside the image
+    T mm = T(0);
+    if (nval > 0) {
+        const T* sp = scr + (size_t)tile * SCR_WORDS + lane0;
+        const T* ref = static_cast<const T*>(A.state_out) + (size_t)tile * TILE_WORDS + lane0;
+        if (grp == 0) {
+#pragma unroll
+            for (int q = 0; q < 35; ++q) check_main_output<T, NV>(sp, ref, q, nval, mm);
+#pragma unroll
+            for (int q = 143; q < hw::N_OUT; ++q) check_main_output<T, NV>(sp, ref, q, nval, mm);
+        } else {
+            const int k = grp - 1;
+            bool has[NV];
+            for (int j = 0; j < NV; ++j) {
+                const int u = u0 + j;
+                has[j] = k == 0 ? u > 0 : (k == 1 ? u + 1 < g.W : (k == 2 ? v > 0 : v + 1 < g.H));
+            }
+            const T* Lk = sp + (SCR_FWD + 27 * k) * TILE_PX;
+            const T* rk = ref + (35 + 27 * k) * TILE_PX;
+#pragma unroll
+            for (int p = 0; p < 21; ++p) {
+                T y[NV], r[NV];
+                ld16(Lk + p * TILE_PX, y);
+                ld16(rk + p * TILE_PX, r);
+                for (int j = 0; j < NV; ++j) {
+                    const T yj = has[j] ? y[j] : T(0);
+                    if (j < nval) check_value(yj, v_abs(yj) > T(1) ? v_abs(yj) : T(1), r[j], mm);
+                }
+            }
+            T tau[6][NV];
+            for (int cc = 0; cc < 6; ++cc) ld16(sp + (SCR_MAIN + hw::MO_TAU + cc) * TILE_PX, tau[cc]);
+#pragma unroll
+            for (int rr = 0; rr < 6; ++rr) {
+                T Lr[6][NV], er[NV], r[NV];
+                for (int cc = 0; cc < 6; ++cc) ld16(Lk + pidx(rr, cc) * TILE_PX, Lr[cc]);
+                ld16(Lk + (21 + rr) * TILE_PX, er);
+                ld16(rk + (21 + rr) * TILE_PX, r);
+                for (int j = 0; j < NV; ++j) {
+                    T Lrow[6], tj[6], y, sc;
+                    for (int cc = 0; cc < 6; ++cc) {
+                        Lrow[cc] = Lr[cc][j];
+                        tj[cc] = tau[cc][j];
+                    }
+                    hw::projected_eta_row(Lrow, er[j], tj, &y, &sc);
+                    if (!has[j]) {
+                        y = T(0);
+                        sc = T(1);
+                    }
+                    if (j < nval) check_value(y, sc, r[j], mm);
+                }
+            }
+        }
+    }
+    __shared__ T wm[(5 * TPR + 31) / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const T x = __shfl_xor_sync(0xffffffffu, mm, o);
+        mm = x > mm ? x : mm;
+    }
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mm = wm[w] > mm ? wm[w] : mm;
+        if (mm > T(0)) atomic_max_nonneg(A.mismatch, double(mm));
+    }
+}
+
+// Pose stage (last): the pixel's xi adjoint from the (R, t) adjoints of its Exp.
 template <typename T>
 __global__ void __launch_bounds__(TILE_PX) k_adjoint_pose(const AdjArgs A, const T* __restrict__ scr) {
     const int tile = blockIdx.x, lane = threadIdx.x;
@@ -307,13 +480,13 @@ __global__ void __launch_bounds__(TILE_PX) k_adjoint_pose(const AdjArgs A, const
     hw::PixCtx<T> c;
     int u, v;
     if (!pixel_context(A, tile, lane, c, io, &u, &v)) return;
-    const T* sp = scr + (size_t)tile * SCR_WORDS + lane;
+    io.scr_in = scr + (size_t)tile * SCR_WORDS + lane;
     T xi[6], Rb[9], tb[3], xib[6];
     for (int q = 0; q < 6; ++q) xi[q] = io.mu(q);
-    for (int q = 0; q < 9; ++q) Rb[q] = sp[(SCR_RB + q) * TILE_PX];
-    for (int q = 0; q < 3; ++q) tb[q] = sp[(SCR_TB + q) * TILE_PX];
-    for (int q = 0; q < 6; ++q) xib[q] = sp[(SCR_XIB + q) * TILE_PX];
-    hw::pose_vjp(io, xi, Rb, tb, xib, sp[SCR_DB * TILE_PX]);
+    for (int q = 0; q < 9; ++q) Rb[q] = io.main_in(hw::MO_RB + q);
+    for (int q = 0; q < 3; ++q) tb[q] = io.main_in(hw::MO_TB + q);
+    for (int q = 0; q < 6; ++q) xib[q] = io.main_in(hw::MO_XIB + q);
+    hw::pose_vjp(io, xi, Rb, tb, xib, io.main_in(hw::MO_DB));
 }
 
 // max |a[i]| over finite values, in the adjoint's own precision, with 16-byte
@@ -348,12 +521,17 @@ __global__ void k_adjoint_exponent(double* scale) {
 
 }  // namespace
 
-cudaError_t launch_adjoint_absmax(const void* a, size_t n, int adj64, double* scale, cudaStream_t st) {
-    unsigned long long* mx = reinterpret_cast<unsigned long long*>(scale + 1);
+// blocks for a grid-stride kernel: 8 blocks of 256 threads per SM
+static int stride_blocks() {
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int blocks = (sms > 0 ? sms : 152) * 8;  // 8 blocks of 256 threads per SM
+    return (sms > 0 ? sms : 152) * 8;
+}
+
+cudaError_t launch_adjoint_absmax(const void* a, size_t n, int adj64, double* scale, cudaStream_t st) {
+    unsigned long long* mx = reinterpret_cast<unsigned long long*>(scale + 1);
+    const int blocks = stride_blocks();
     if (adj64)
         k_adjoint_absmax<double, double2><<<blocks, 256, 0, st>>>(static_cast<const double2*>(a), n / 2, mx);
     else
@@ -378,12 +556,14 @@ size_t adjoint_scratch_bytes(int n_tiles, int state64) {
 template <typename T>
 static cudaError_t launch_hw(const AdjArgs& A, int n_tiles, void* scratch, cudaStream_t st) {
     T* scr = static_cast<T*>(scratch);
-    k_adjoint_fwd<T><<<dim3(n_tiles, 4), TILE_PX, 0, st>>>(A, scr);
+    k_adjoint_fwd<T><<<dim3(n_tiles, TILE_H), TILE_PX, 0, st>>>(A, scr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_adjoint_main<T><<<n_tiles, TILE_PX, 0, st>>>(A, scr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_adjoint_dir<T><<<dim3(n_tiles, 4), TILE_PX, 0, st>>>(A, scr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_adjoint_check<T><<<n_tiles, 5 * TILE_PX / (16 / sizeof(T)), 0, st>>>(A, scr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_adjoint_pose<T><<<n_tiles, TILE_PX, 0, st>>>(A, scr);
     return cudaGetLastError();

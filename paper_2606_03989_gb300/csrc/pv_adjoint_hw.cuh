@@ -287,12 +287,15 @@ constexpr int N_OUT = 151; // output planes, in state order
 //   T nb(k, q)                      neighbour value q (NB_*) of direction k
 //   T I_s(), tap(q)                 source intensity; I_t, g_x, g_y taps (4 each)
 //   T ybar(q)                       adjoint of output plane q (state order)
-//   void identity_forward(k, R, t, L, e)  the damped identity message of
-//                                   direction k (damped_identity, or precomputed)
-//   T damped(k, q)                  value q (Lambda packed, eta) of that message
-//                                   again, for a direction with a neighbour
-//   void main_out(p, v)             what the main stage hands on (plane p, MO_*)
-//   T main_in(p)                    that value back (pixel_vjp only)
+//   void identity_sums(R, t, L, e)  sums over the directions with a neighbour of
+//                                   the damped identity messages (Lambda packed,
+//                                   eta) into the pixel at pose (R, t)
+//   void identity_eta_adj(w)        sum over them of Lambda_k times the adjoint
+//                                   of the projected eta_k' (w_k below)
+//   T damped(k, q)                  value q (Lambda packed, eta) of the damped
+//                                   message of direction k (with a neighbour)
+//   void main_out(p, v), T main_in(p)  what the main stage hands on (plane p,
+//                                   MO_*), and that value back
 //   void out(q, y, scale)           recomputed output plane q and the magnitude
 //                                   of the terms it is formed from (>= 1, >= |y|)
 //   void add_mu/add_msg/add_nm/add_nb/add_Is/add_tap(..., v), add_lamD/add_isD/
@@ -435,8 +438,7 @@ PV_HD void photometric(T d, T I_s, const T* tap, const PixCtx<T>& c, const T* R,
 
 // The damped identity message of direction k into the pixel at pose (R, t):
 // Lambda (packed) and eta, from the neighbour's values and the pixel's old
-// message of slot k (an I/O object's identity_forward may compute it with this,
-// or return it precomputed).
+// message of slot k.
 template <typename T, typename IO>
 PV_HD void damped_identity(IO& io, const PixCtx<T>& c, int k, const T* R, const T* t, T* L, T* e) {
     const T beta = c.beta, omb = T(1) - c.beta;
@@ -448,19 +450,47 @@ PV_HD void damped_identity(IO& io, const PixCtx<T>& c, int k, const T* R, const 
     for (int q = 0; q < 21; ++q) L[q] = omb * Ln[q] + beta * io.msg(k, q);
 }
 
-// What the main stage of the reverse pass hands to the per-direction and pose
-// stages (planes of io.main_out): the adjoints of the damped identity message of
-// each direction with a neighbour (27 k + q: Lambda packed, eta), of the pixel's
-// rotation and translation (R, t = Exp(xi)), of xi through the prior, and of the
-// log-depth.
-constexpr int MO_MSG = 0, MO_RB = 108, MO_TB = 117, MO_XIB = 120, MO_DB = 126;
-constexpr int MO_PLANES = 127;
+// The adjoint of the projected eta_k' = eta_k - Lambda_k tau reaches tau as
+// -Lambda_k ybar(eta_k'): w_k = Lambda_k ybar(eta_k') (an I/O object's
+// identity_eta_adj sums it over the directions). identity_sums_direct computes
+// both sums from the damped messages (for an I/O object without a forward stage
+// of its own).
+template <typename T, typename IO>
+PV_HD void identity_w(IO& io, int k, const T* L, T* w) {
+    T eyb[6];
+    for (int r = 0; r < 6; ++r) eyb[r] = io.ybar(35 + 27 * k + 21 + r);
+    sym_mv(L, eyb, w);
+}
 
-// Main stage: the update's outputs (through io.out), and the reverse pass of
-// everything but the identity messages and the final Exp(xi); the adjoints of
-// the inputs it reaches go through io.add_*, the rest through io.main_out. The
-// damped identity messages are not kept: they are read again (io.damped) where
-// the output check and the reverse pass need them.
+template <typename T, typename IO>
+PV_HD void identity_sums_direct(IO& io, const PixCtx<T>& c, const T* R, const T* t, T* Ls, T* es, T* ws) {
+    for (int q = 0; q < 21; ++q) Ls[q] = T(0);
+    for (int q = 0; q < 6; ++q) es[q] = ws[q] = T(0);
+    for (int k = 0; k < 4; ++k) {
+        if (!c.has[k]) continue;
+        T L[21], e[6], w[6];
+        damped_identity(io, c, k, R, t, L, e);
+        identity_w(io, k, L, w);
+        for (int q = 0; q < 21; ++q) Ls[q] += L[q];
+        for (int q = 0; q < 6; ++q) {
+            es[q] += e[q];
+            ws[q] += w[q];
+        }
+    }
+}
+
+// What the main stage of the reverse pass hands to the per-direction and pose
+// stages (planes of io.main_out): the update tau and the adjoints of M_p and of
+// eta_b (from which each direction forms its damped message's adjoint), of the
+// pixel's rotation and translation (R, t = Exp(xi)), of xi through the prior, and
+// of the log-depth.
+constexpr int MO_TAU = 0, MO_MPB = 7, MO_EBB = 28, MO_RB = 34, MO_TB = 43, MO_XIB = 46, MO_DB = 52;
+constexpr int MO_PLANES = 53;
+
+// Main stage: the update's outputs but the identity messages' (through io.out),
+// and the reverse pass of everything but the identity messages and the final
+// Exp(xi); the adjoints of the inputs it reaches go through io.add_*, the rest
+// through io.main_out. The damped identity messages enter only as their sums.
 template <typename T, typename IO>
 PV_HD void pixel_vjp_main(IO& io, const PixCtx<T>& c) {
     const T lam_R = c.lam_R, beta = c.beta, omb = T(1) - c.beta;
@@ -479,12 +509,11 @@ PV_HD void pixel_vjp_main(IO& io, const PixCtx<T>& c) {
     }
     T md = c.lam_Z;
     eb[6] -= c.lam_Z * (d - c.d_prior);
-    for (int k = 0; k < 4; ++k) {
-        if (!c.has[k]) continue;
-        T L[21], e[6];  // the damped identity message
-        io.identity_forward(k, R, t, L, e);
-        for (int q = 0; q < 6; ++q) eb[q] += e[q];
-        for (int q = 0; q < 21; ++q) Mp[q] += L[q];
+    {
+        T Ls[21], es[6];  // the damped identity messages, summed
+        io.identity_sums(R, t, Ls, es);
+        for (int q = 0; q < 6; ++q) eb[q] += es[q];
+        for (int q = 0; q < 21; ++q) Mp[q] += Ls[q];
     }
     T nl[4], ne[4];
     for (int k = 0; k < 4; ++k) {
@@ -553,18 +582,6 @@ PV_HD void pixel_vjp_main(IO& io, const PixCtx<T>& c) {
     for (int q = 0; q < 6; ++q) out_plain(28 + q, sb * J[q]);
     out_plain(34, md + v_div(alpha * J[6] * J[6], es));
     for (int k = 0; k < 4; ++k) {
-        T L[21], el[6];
-        for (int q = 0; q < 21; ++q) L[q] = c.has[k] ? io.damped(k, q) : T(0);
-        for (int q = 0; q < 6; ++q) el[q] = c.has[k] ? io.damped(k, 21 + q) : T(0);
-        for (int q = 0; q < 21; ++q) out_plain(35 + 27 * k + q, L[q]);
-        for (int r = 0; r < 6; ++r) {
-            T e = el[r], m = v_abs(el[r]);
-            for (int cc = 0; cc < 6; ++cc) {
-                e -= L[pidx(r, cc)] * tau[cc];
-                m += v_abs(L[pidx(r, cc)] * tau[cc]);
-            }
-            io.out(35 + 27 * k + 21 + r, e, m > v_abs(e) ? (m > T(1) ? m : T(1)) : (v_abs(e) > T(1) ? v_abs(e) : T(1)));
-        }
         out_plain(143 + 2 * k, nl[k]);
         const T e = ne[k] - nl[k] * tau[6];
         const T m = v_abs(ne[k]) + v_abs(nl[k] * tau[6]);
@@ -581,15 +598,14 @@ PV_HD void pixel_vjp_main(IO& io, const PixCtx<T>& c) {
     for (int q = 0; q < 9; ++q) Rb[q] = T(0);
     for (int q = 0; q < 3; ++q) tb[q] = T(0);
     // projected messages eta' = eta - Lambda tau (the adjoints of the damped
-    // messages themselves are formed at the end), and the normal ones
+    // messages themselves are formed per direction), and the normal ones
+    {
+        T ws[6];
+        io.identity_eta_adj(ws);
+        for (int q = 0; q < 6; ++q) taub[q] -= ws[q];
+    }
     T nlb[4], neb[4];
     for (int k = 0; k < 4; ++k) {
-        T eyb[6], L[21];
-        for (int r = 0; r < 6; ++r) eyb[r] = io.ybar(35 + 27 * k + 21 + r);
-        for (int q = 0; q < 21; ++q) L[q] = c.has[k] ? io.damped(k, q) : T(0);
-        T tmp[6];
-        sym_mv(L, eyb, tmp);
-        for (int q = 0; q < 6; ++q) taub[q] -= tmp[q];
         const T nyb = io.ybar(143 + 2 * k), eyn = io.ybar(144 + 2 * k);
         nlb[k] = nyb - eyn * tau[6];
         neb[k] = eyn;
@@ -797,30 +813,63 @@ PV_HD void pixel_vjp_main(IO& io, const PixCtx<T>& c) {
         io.add_nb(k, NB_DJ, -rnb);
     }
     io.add_lamN(lamNb);
-    // the damped identity messages: their adjoints from the projected outputs
-    // (Lambda' = Lambda, eta' = eta - Lambda tau) and from M_p and eta_b; own
-    // old messages (damping)
-    for (int k = 0; k < 4; ++k) {
-        if (!c.has[k]) continue;
-        T Lb[21], eyb[6];
-        for (int q = 0; q < 21; ++q) Lb[q] = io.ybar(35 + 27 * k + q);
-        for (int r = 0; r < 6; ++r) eyb[r] = io.ybar(35 + 27 * k + 21 + r);
-        add_packed_outer(eyb, tau, T(-1), Lb);
-        for (int q = 0; q < 21; ++q) {
-            const T v = Lb[q] + Mpb[q];
-            io.main_out(MO_MSG + 27 * k + q, v);
-            io.add_msg(k, q, beta * v);
-        }
-        for (int q = 0; q < 6; ++q) {
-            const T v = eyb[q] + ebb[q];
-            io.main_out(MO_MSG + 27 * k + 21 + q, v);
-            io.add_msg(k, 21 + q, beta * v);
-        }
-    }
+    for (int q = 0; q < 7; ++q) io.main_out(MO_TAU + q, tau[q]);
+    for (int q = 0; q < 21; ++q) io.main_out(MO_MPB + q, Mpb[q]);
+    for (int q = 0; q < 6; ++q) io.main_out(MO_EBB + q, ebb[q]);
     for (int q = 0; q < 9; ++q) io.main_out(MO_RB + q, Rb[q]);
     for (int q = 0; q < 3; ++q) io.main_out(MO_TB + q, tb[q]);
     for (int q = 0; q < 6; ++q) io.main_out(MO_XIB + q, xib[q]);
     io.main_out(MO_DB, db);
+}
+
+// Row r of a projected identity message, eta_r' = eta_r - sum_c Lambda_rc tau_c
+// (Lrow: Lambda_r0 .. Lambda_r5), and the magnitude of the terms it is formed
+// from, as the recompute check's scale (>= 1, >= |eta_r'|).
+template <typename T>
+PV_HD void projected_eta_row(const T* Lrow, T er, const T* tau, T* y, T* scale) {
+    T e = er, m = v_abs(er);
+    for (int cc = 0; cc < 6; ++cc) {
+        e -= Lrow[cc] * tau[cc];
+        m += v_abs(Lrow[cc] * tau[cc]);
+    }
+    *y = e;
+    *scale = m > v_abs(e) ? (m > T(1) ? m : T(1)) : (v_abs(e) > T(1) ? v_abs(e) : T(1));
+}
+
+// The outputs of the damped identity message of direction k (Lambda' = Lambda,
+// eta' = eta - Lambda tau; zero without a neighbour), through io.out.
+template <typename T, typename IO>
+PV_HD void identity_outputs(IO& io, const PixCtx<T>& c, int k, const T* tau) {
+    T L[21], el[6];
+    for (int q = 0; q < 21; ++q) L[q] = c.has[k] ? io.damped(k, q) : T(0);
+    for (int q = 0; q < 6; ++q) el[q] = c.has[k] ? io.damped(k, 21 + q) : T(0);
+    for (int q = 0; q < 21; ++q) io.out(35 + 27 * k + q, L[q], v_abs(L[q]) > T(1) ? v_abs(L[q]) : T(1));
+    for (int r = 0; r < 6; ++r) {
+        T Lrow[6], y, sc;
+        for (int cc = 0; cc < 6; ++cc) Lrow[cc] = L[pidx(r, cc)];
+        projected_eta_row(Lrow, el[r], tau, &y, &sc);
+        io.out(35 + 27 * k + 21 + r, y, sc);
+    }
+}
+
+// The adjoint of the damped identity message of direction k (Lbar packed, ebar)
+// from those of its outputs and of M_p and eta_b (Mpb, ebb); the pixel's own old
+// message of slot k enters it (damping) through io.add_msg.
+template <typename T, typename IO>
+PV_HD void identity_msg_adjoint(IO& io, const PixCtx<T>& c, int k, const T* tau, const T* Mpb, const T* ebb, T* Lb,
+                                T* eb) {
+    T eyb[6];
+    for (int q = 0; q < 21; ++q) Lb[q] = io.ybar(35 + 27 * k + q);
+    for (int r = 0; r < 6; ++r) eyb[r] = io.ybar(35 + 27 * k + 21 + r);
+    add_packed_outer(eyb, tau, T(-1), Lb);
+    for (int q = 0; q < 21; ++q) {
+        Lb[q] += Mpb[q];
+        io.add_msg(k, q, c.beta * Lb[q]);
+    }
+    for (int q = 0; q < 6; ++q) {
+        eb[q] = eyb[q] + ebb[q];
+        io.add_msg(k, 21 + q, c.beta * eb[q]);
+    }
 }
 
 // Per-direction stage: the reverse pass of the identity message of direction k
@@ -940,17 +989,20 @@ PV_HD void pose_vjp(IO& io, const T* xi, const T* Rb, const T* tb, const T* xib_
 template <typename T, typename IO>
 PV_HD void pixel_vjp(IO& io, const PixCtx<T>& c) {
     pixel_vjp_main(io, c);
-    T xi[6], R[9], t[3], Rb[9], tb[3], xib[6];
+    T xi[6], R[9], t[3], Rb[9], tb[3], xib[6], tau[7], Mpb[21], ebb[6];
     for (int q = 0; q < 6; ++q) xi[q] = io.mu(q);
     se3_exp(xi, R, t);
+    for (int q = 0; q < 7; ++q) tau[q] = io.main_in(MO_TAU + q);
+    for (int q = 0; q < 21; ++q) Mpb[q] = io.main_in(MO_MPB + q);
+    for (int q = 0; q < 6; ++q) ebb[q] = io.main_in(MO_EBB + q);
     for (int q = 0; q < 9; ++q) Rb[q] = io.main_in(MO_RB + q);
     for (int q = 0; q < 3; ++q) tb[q] = io.main_in(MO_TB + q);
     for (int q = 0; q < 6; ++q) xib[q] = io.main_in(MO_XIB + q);
     for (int k = 0; k < 4; ++k) {
+        identity_outputs(io, c, k, tau);
         if (!c.has[k]) continue;
         T Lb[21], eb[6];
-        for (int q = 0; q < 21; ++q) Lb[q] = io.main_in(MO_MSG + 27 * k + q);
-        for (int q = 0; q < 6; ++q) eb[q] = io.main_in(MO_MSG + 27 * k + 21 + q);
+        identity_msg_adjoint(io, c, k, tau, Mpb, ebb, Lb, eb);
         identity_vjp(io, c, k, R, t, Lb, eb, Rb, tb);
     }
     pose_vjp(io, xi, Rb, tb, xib, io.main_in(MO_DB));
