@@ -319,8 +319,9 @@ __global__ void __launch_bounds__(TILE_PX, sizeof(T) == 4 ? PV_ADJ_MAIN_BLOCKS :
 // the damping's adjoint into the pixel's old message, the reverse pass of the
 // message (scattering the neighbour's adjoints), and the pose's (R, t) adjoints
 // added to the scratch.
+// (FP32 at 4 blocks per SM, 128 registers: faster than 3 blocks at 168)
 template <typename T>
-__global__ void __launch_bounds__(TILE_PX) k_adjoint_dir(const AdjArgs A, T* __restrict__ scr) {
+__global__ void __launch_bounds__(TILE_PX, sizeof(T) == 4 ? 4 : 1) k_adjoint_dir(const AdjArgs A, T* __restrict__ scr) {
     const int tile = blockIdx.x, lane = threadIdx.x, k = blockIdx.y;
     KernelIO<T> io;
     hw::PixCtx<T> c;

@@ -893,34 +893,50 @@ PV_HD void identity_vjp(IO& io, const PixCtx<T>& c, int k, const T* R, const T* 
     }
     solve_C(L, z, iuz, uj, eb_, wv);
     for (int q = 0; q < 6; ++q) wv[q] *= lam_R;
-    // C_bar = lam_R^2 C^-1 G C^-1 - w y^T (full matrix)
-    T G[36], X[36], Cb[36];
+    // C_bar = lam_R^2 C^-1 G C^-1 - w y^T, G the symmetric matrix form of the
+    // adjoint of Lambda (off-diagonals halved). Only C_bar + C_bar^T reaches W
+    // (W_bar[p(r,c)] = C_bar_rc + C_bar_cr, diagonal C_bar_rr) and u (u_bar =
+    // (C_bar + C_bar^T) u). M = C^-1 G C^-1 is symmetric: formed from C^-1
+    // (six solves on the unit vectors) column by column.
+    T Ci[21], M[21];
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) {
+        T ec[6], o[6];
+        for (int r = 0; r < 6; ++r) ec[r] = r == cc ? T(1) : T(0);
+        solve_C(L, z, iuz, uj, ec, o);
+        for (int r = cc; r < 6; ++r) Ci[pidx(r, cc)] = o[r];
+    }
     {
-        T Lnb[21];
-        for (int q = 0; q < 21; ++q) Lnb[q] = omb * Lbar[q];
-        full_from_packed_adjoint(Lnb, G);
+        T Gp[21];
+        for (int r = 0; r < 6; ++r)
+            for (int c2 = 0; c2 <= r; ++c2) Gp[pidx(r, c2)] = (r == c2 ? omb : T(0.5) * omb) * Lbar[pidx(r, c2)];
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) {
+            T P[6];  // column cc of G C^-1
+            for (int a = 0; a < 6; ++a) {
+                T acc = T(0);
+                for (int b = 0; b < 6; ++b) acc += Gp[pidx(a, b)] * Ci[pidx(b, cc)];
+                P[a] = acc;
+            }
+            for (int r = cc; r < 6; ++r) {
+                T acc = T(0);
+                for (int a = 0; a < 6; ++a) acc += Ci[pidx(r, a)] * P[a];
+                M[pidx(r, cc)] = acc;
+            }
+        }
     }
-    for (int cc = 0; cc < 6; ++cc) {  // X = C^-1 G (columns)
-        T col[6], o[6];
-        for (int r = 0; r < 6; ++r) col[r] = G[6 * r + cc];
-        solve_C(L, z, iuz, uj, col, o);
-        for (int r = 0; r < 6; ++r) X[6 * r + cc] = o[r];
-    }
-    for (int r = 0; r < 6; ++r) {  // Cb = lam_R^2 X C^-1 = lam_R^2 (C^-1 X^T)^T
-        T row[6], o[6];
-        for (int cc = 0; cc < 6; ++cc) row[cc] = X[6 * r + cc];
-        solve_C(L, z, iuz, uj, row, o);
-        for (int cc = 0; cc < 6; ++cc) Cb[6 * r + cc] = lam_R * lam_R * o[cc] - wv[r] * yv[cc];
-    }
-    // C = W + lam_R I + u u^T
-    T Wb[21];
-    for (int q = 0; q < 21; ++q) Wb[q] = T(0);
-    add_packed_from_full(Cb, T(1), Wb);
-    T ub[6];
-    for (int r = 0; r < 6; ++r) {
-        T acc = T(0);
-        for (int cc = 0; cc < 6; ++cc) acc += (Cb[6 * r + cc] + Cb[6 * cc + r]) * uj[cc];
-        ub[r] = acc;
+    T Wb[21], ub[6];
+    for (int r = 0; r < 6; ++r) ub[r] = T(0);
+    {
+        const T l2 = lam_R * lam_R;
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+            for (int c2 = 0; c2 <= r; ++c2) {
+                const T sc = T(2) * l2 * M[pidx(r, c2)] - (wv[r] * yv[c2] + wv[c2] * yv[r]);  // C_bar_rc + C_bar_cr
+                Wb[pidx(r, c2)] = r == c2 ? T(0.5) * sc : sc;
+                ub[r] += sc * uj[c2];
+                if (r != c2) ub[c2] += sc * uj[r];
+            }
     }
     // q = g0 - u (u^T rb), g0 = -eta_J - W rb; q_bar = w
     T urb = T(0), uw = T(0);
