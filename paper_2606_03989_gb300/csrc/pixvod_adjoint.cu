@@ -22,6 +22,9 @@ __device__ __forceinline__ T ld(const void* p, size_t i) {
 // lane). Regions:
 //   SCR_FWD   the damped identity messages (direction k at 27 k: Lambda
 //             packed, eta), from k_adjoint_fwd, read by k_adjoint_dir;
+//   SCR_IDF   what the reverse pass of each identity message needs from its
+//             forward (hw::IdFwd: direction k at ID_FWD_VALS k), from
+//             k_adjoint_fwd, read by k_adjoint_dir;
 //   SCR_SUM   their sums over the directions (Lambda 21, eta 6) and the sum of
 //             Lambda_k ybar(eta_k') (6), from k_adjoint_fwd, read by the main
 //             stage;
@@ -34,7 +37,8 @@ __device__ __forceinline__ T ld(const void* p, size_t i) {
 // No kernel loads a plane that it writes (its loads take the read-only path and
 // need not wait for its stores and atomics).
 constexpr int SCR_FWD = 0;
-constexpr int SCR_SUM = SCR_FWD + 108;
+constexpr int SCR_IDF = SCR_FWD + 108;
+constexpr int SCR_SUM = SCR_IDF + 4 * hw::ID_FWD_VALS;
 constexpr int SCR_MAIN = SCR_SUM + 33;
 constexpr int SCR_CHK = SCR_MAIN + hw::MO_PLANES;
 constexpr int SCR_CHK_S = SCR_CHK + 43;
@@ -211,10 +215,20 @@ __global__ void __launch_bounds__(TILE_PX) k_adjoint_fwd(const AdjArgs A, T* __r
         T xi[6], R[9], t[3];
         for (int q = 0; q < 6; ++q) xi[q] = io.mu(q);
         se3_exp(xi, R, t);
-        hw::damped_identity(io, c, k, R, t, L, e);
+        hw::IdFwd<T> f;
+        hw::damped_identity(io, c, k, R, t, L, e, &f);
         hw::identity_w(io, k, L, w);
         for (int q = 0; q < 21; ++q) sp[(SCR_FWD + 27 * k + q) * TILE_PX] = L[q];
         for (int q = 0; q < 6; ++q) sp[(SCR_FWD + 27 * k + 21 + q) * TILE_PX] = e[q];
+        T* fp = sp + (SCR_IDF + hw::ID_FWD_VALS * k) * TILE_PX;
+        for (int q = 0; q < 6; ++q) {
+            fp[q * TILE_PX] = f.rb[q];
+            fp[(48 + q) * TILE_PX] = f.en[q];
+        }
+        for (int q = 0; q < 21; ++q) {
+            fp[(6 + q) * TILE_PX] = f.W[q];
+            fp[(27 + q) * TILE_PX] = f.Ci[q];
+        }
     }
     for (int o = 1; o < 4; o <<= 1) {
         for (int q = 0; q < 21; ++q) L[q] += __shfl_xor_sync(0xffffffffu, L[q], o);
@@ -344,7 +358,19 @@ __global__ void __launch_bounds__(TILE_PX, sizeof(T) == 4 ? 4 : 1) k_adjoint_dir
     se3_exp(xi, R, t);
     for (int q = 0; q < 9; ++q) Rb[q] = T(0);
     for (int q = 0; q < 3; ++q) tb[q] = T(0);
-    hw::identity_vjp(io, c, k, R, t, Lb, eb, Rb, tb);
+    hw::IdFwd<T> f;
+    {
+        const T* fp = sp + (SCR_IDF + hw::ID_FWD_VALS * k) * TILE_PX;
+        for (int q = 0; q < 6; ++q) {
+            f.rb[q] = __ldg(fp + q * TILE_PX);
+            f.en[q] = __ldg(fp + (48 + q) * TILE_PX);
+        }
+        for (int q = 0; q < 21; ++q) {
+            f.W[q] = __ldg(fp + (6 + q) * TILE_PX);
+            f.Ci[q] = __ldg(fp + (27 + q) * TILE_PX);
+        }
+    }
+    hw::identity_vjp(io, c, k, R, t, f, Lb, eb, Rb, tb);
     for (int q = 0; q < 9; ++q) atomicAdd(sp + (SCR_MAIN + hw::MO_RB + q) * TILE_PX, Rb[q]);
     for (int q = 0; q < 3; ++q) atomicAdd(sp + (SCR_MAIN + hw::MO_TB + q) * TILE_PX, tb[q]);
 }

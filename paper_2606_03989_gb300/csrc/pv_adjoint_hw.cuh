@@ -436,11 +436,34 @@ PV_HD void photometric(T d, T I_s, const T* tap, const PixCtx<T>& c, const T* R,
     *rph = P.r;
 }
 
+// What the reverse pass of an identity message needs from its forward: the
+// residual rb, W = M_p,j - Lambda_j->i, C^-1 (packed; C = W + lam_R I + u u^T)
+// and eta_new (ID_FWD_VALS values, in this order).
+template <typename T>
+struct IdFwd {
+    T rb[6], W[21], Ci[21], en[6];
+};
+constexpr int ID_FWD_VALS = 54;
+
+// C^-1 (packed) from the factor of A = W + lam_R I, z = A^-1 u, 1/(1 + u^T z):
+// six solves on the unit vectors
+template <typename T>
+PV_HD void form_Ci(const T* L, const T* z, T iuz, const T* u, T* Ci) {
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) {
+        T ec[6], o[6];
+        for (int r = 0; r < 6; ++r) ec[r] = r == cc ? T(1) : T(0);
+        solve_C(L, z, iuz, u, ec, o);
+        for (int r = cc; r < 6; ++r) Ci[pidx(r, cc)] = o[r];
+    }
+}
+
 // The damped identity message of direction k into the pixel at pose (R, t):
 // Lambda (packed) and eta, from the neighbour's values and the pixel's old
-// message of slot k.
+// message of slot k; with f, also what its reverse pass needs.
 template <typename T, typename IO>
-PV_HD void damped_identity(IO& io, const PixCtx<T>& c, int k, const T* R, const T* t, T* L, T* e) {
+PV_HD void damped_identity(IO& io, const PixCtx<T>& c, int k, const T* R, const T* t, T* L, T* e,
+                           IdFwd<T>* f = nullptr) {
     const T beta = c.beta, omb = T(1) - c.beta;
     T nbk[NB_VALS];
     for (int q = 0; q < NB_VALS; ++q) nbk[q] = io.nb(k, q);
@@ -448,6 +471,14 @@ PV_HD void damped_identity(IO& io, const PixCtx<T>& c, int k, const T* R, const 
     identity_message(nbk, R, t, c.lam_R, rb, W, Lc, z, &iuz, Ln, en);
     for (int q = 0; q < 6; ++q) e[q] = omb * en[q] + beta * io.msg(k, 21 + q);
     for (int q = 0; q < 21; ++q) L[q] = omb * Ln[q] + beta * io.msg(k, q);
+    if (f) {
+        for (int q = 0; q < 6; ++q) {
+            f->rb[q] = rb[q];
+            f->en[q] = en[q];
+        }
+        for (int q = 0; q < 21; ++q) f->W[q] = W[q];
+        form_Ci(Lc, z, iuz, nbk + NB_U, f->Ci);
+    }
 }
 
 // The adjoint of the projected eta_k' = eta_k - Lambda_k tau reaches tau as
@@ -877,35 +908,31 @@ PV_HD void identity_msg_adjoint(IO& io, const PixCtx<T>& c, int k, const T* tau,
 // adjoints of its damped value (Lbar packed, ebar); adds the adjoints of the
 // neighbour's values through io.add_nb and the pose's to (Rb, tb).
 template <typename T, typename IO>
-PV_HD void identity_vjp(IO& io, const PixCtx<T>& c, int k, const T* R, const T* t, const T* Lbar, const T* ebar,
-                        T* Rb, T* tb) {
+PV_HD void identity_vjp(IO& io, const PixCtx<T>& c, int k, const T* R, const T* t, const IdFwd<T>& f,
+                        const T* Lbar, const T* ebar, T* Rb, T* tb) {
     const T lam_R = c.lam_R, omb = T(1) - c.beta;
-    T nbk[NB_VALS];
-    for (int q = 0; q < NB_VALS; ++q) nbk[q] = io.nb(k, q);
-    T rb[6], W[21], L[21], z[6], iuz, Ln[21], en[6];
-    identity_message(nbk, R, t, lam_R, rb, W, L, z, &iuz, Ln, en);
-    const T* uj = nbk + NB_U;
+    const T* rb = f.rb;
+    const T* W = f.W;
+    const T* Ci = f.Ci;
+    T uj[6], xj[6];
+    for (int q = 0; q < 6; ++q) {
+        uj[q] = io.nb(k, NB_U + q);
+        xj[q] = io.nb(k, NB_XJ + q);
+    }
     // y = C^-1 q = eta_new / lam_R; w = lam_R C^-1 eta_new_bar
     T yv[6], wv[6], eb_[6];
     for (int q = 0; q < 6; ++q) {
-        yv[q] = en[q] / lam_R;
+        yv[q] = f.en[q] / lam_R;
         eb_[q] = omb * ebar[q];
     }
-    solve_C(L, z, iuz, uj, eb_, wv);
+    sym_mv(Ci, eb_, wv);
     for (int q = 0; q < 6; ++q) wv[q] *= lam_R;
     // C_bar = lam_R^2 C^-1 G C^-1 - w y^T, G the symmetric matrix form of the
     // adjoint of Lambda (off-diagonals halved). Only C_bar + C_bar^T reaches W
     // (W_bar[p(r,c)] = C_bar_rc + C_bar_cr, diagonal C_bar_rr) and u (u_bar =
-    // (C_bar + C_bar^T) u). M = C^-1 G C^-1 is symmetric: formed from C^-1
-    // (six solves on the unit vectors) column by column.
-    T Ci[21], M[21];
-#pragma unroll
-    for (int cc = 0; cc < 6; ++cc) {
-        T ec[6], o[6];
-        for (int r = 0; r < 6; ++r) ec[r] = r == cc ? T(1) : T(0);
-        solve_C(L, z, iuz, uj, ec, o);
-        for (int r = cc; r < 6; ++r) Ci[pidx(r, cc)] = o[r];
-    }
+    // (C_bar + C_bar^T) u). M = C^-1 G C^-1 is symmetric: formed column by
+    // column.
+    T M[21];
     {
         T Gp[21];
         for (int r = 0; r < 6; ++r)
@@ -959,7 +986,7 @@ PV_HD void identity_vjp(IO& io, const PixCtx<T>& c, int k, const T* R, const T* 
     }
     // rb = Log(Exp(xi_j)^-1 Exp(xi_i))
     T Rj[9], tj[3], Rr[9], tr[3];
-    se3_exp(nbk + NB_XJ, Rj, tj);
+    se3_exp(xj, Rj, tj);
     se3_invmul(Rj, tj, R, t, Rr, tr);
     T Rrb[9], trb[3];
     for (int q = 0; q < 9; ++q) Rrb[q] = T(0);
@@ -984,7 +1011,7 @@ PV_HD void identity_vjp(IO& io, const PixCtx<T>& c, int k, const T* R, const T* 
         tjb[i] = -v;
     }
     T xjb[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    exp_vjp(nbk + NB_XJ, Rjb, tjb, xjb);
+    exp_vjp(xj, Rjb, tjb, xjb);
     for (int q = 0; q < 6; ++q) io.add_nb(k, NB_XJ + q, xjb[q]);
 }
 
@@ -1017,9 +1044,11 @@ PV_HD void pixel_vjp(IO& io, const PixCtx<T>& c) {
     for (int k = 0; k < 4; ++k) {
         identity_outputs(io, c, k, tau);
         if (!c.has[k]) continue;
-        T Lb[21], eb[6];
+        T Lb[21], eb[6], Ld[21], ed[6];
+        IdFwd<T> f;
+        damped_identity(io, c, k, R, t, Ld, ed, &f);
         identity_msg_adjoint(io, c, k, tau, Mpb, ebb, Lb, eb);
-        identity_vjp(io, c, k, R, t, Lb, eb, Rb, tb);
+        identity_vjp(io, c, k, R, t, f, Lb, eb, Rb, tb);
     }
     pose_vjp(io, xi, Rb, tb, xib, io.main_in(MO_DB));
 }
