@@ -260,7 +260,8 @@ pixvod_status pixvod_launch_count(pixvod_handle* h, int64_t* out);
  * constant.
  * Two reverse passes exist (pixvod_set_backward_method):
  *   PIXVOD_ADJOINT_HANDWRITTEN (default): the hand-written reverse pass, in the
- *     handle's precision (FP32 or FP64), one thread per pixel, no tape;
+ *     handle's precision (FP32 or FP64), no tape, in stages with one thread per
+ *     pixel or per pixel and direction;
  *   PIXVOD_ADJOINT_TAPE: a reverse-mode tape of the same update in FP64 (about
  *     230 KB of tape per pixel and sweep, a 10 GB workspace at 320x240), kept to
  *     cross-check the hand-written pass.
