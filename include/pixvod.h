@@ -337,6 +337,11 @@ pixvod_status pixvod_set_backward_window(pixvod_handle* h, int32_t last_sweeps);
  *                            all sequences, blocks meeting at a bounded grid
  *                            barrier between sweeps (blocks_per_sm resident
  *                            blocks per SM, 1..4).
+ * Sequences of the quadtree topology (params.topology) batch too: under
+ * PIXVOD_SCHED_BATCHED a sweep is one launch of each of the three quadtree
+ * kernels (pixels, node messages, node beliefs) for all sequences; the
+ * persistent schedule is for the grid only (a quadtree sweep is three dependent
+ * launches).
  * The keyframe count rule applies to the batch's frame index.
  * --------------------------------------------------------------------------- */
 typedef struct pixvod_batch pixvod_batch;
@@ -350,7 +355,9 @@ pixvod_status pixvod_batch_workspace_bytes(int32_t n, const pixvod_intrinsics* K
                                            size_t* out_bytes);
 
 /* Create a batch on a caller-owned 256-byte aligned workspace (as pixvod_create).
- * The schedule starts as PIXVOD_SCHED_PERSISTENT with 4 blocks per SM.
+ * The schedule starts as PIXVOD_SCHED_PERSISTENT with 4 blocks per SM (grid
+ * sequences, where the device supports cooperative launches), else
+ * PIXVOD_SCHED_BATCHED.
  * Synchronises the stream. EINVAL / ENOMEM as pixvod_create; n >= 1. */
 pixvod_status pixvod_batch_create(int32_t n, const pixvod_intrinsics* K, const pixvod_params* p, void* d_workspace,
                                   size_t ws_bytes, void* stream, pixvod_batch** out);
@@ -380,7 +387,8 @@ pixvod_status pixvod_batch_state_size(pixvod_batch* b, int32_t i, size_t* bytes)
 pixvod_status pixvod_batch_save_state(pixvod_batch* b, int32_t i, void* h_buf, size_t bytes);
 
 /* Choose the schedule (and blocks per SM for the persistent one, 1..4, clamped
- * to what the device can hold resident). EINVAL on an unknown schedule. */
+ * to what the device can hold resident). EINVAL on an unknown schedule, and on
+ * the persistent one for quadtree sequences. */
 pixvod_status pixvod_batch_set_schedule(pixvod_batch* b, int32_t schedule, int32_t blocks_per_sm);
 pixvod_status pixvod_batch_get_schedule(pixvod_batch* b, int32_t* schedule, int32_t* blocks_per_sm);
 
@@ -390,7 +398,9 @@ pixvod_status pixvod_batch_get_schedule(pixvod_batch* b, int32_t* schedule, int3
  * keyframe state. Valid right after the first pixvod_batch_track (frame index 1)
  * while the registered frame buffers still hold the keyframes (ESTATE
  * otherwise). Synchronises. times_ms (optional, 5 entries) receives the mean
- * time per run of each candidate in that order. */
+ * time per run of each candidate in that order (-1 for a candidate not tried:
+ * more blocks per SM than the device holds, or any persistent one for quadtree
+ * sequences). */
 pixvod_status pixvod_batch_autotune(pixvod_batch* b, int32_t n_iters, int32_t reps, float* times_ms);
 
 /* Kernels the batch has launched since creation. */

@@ -52,8 +52,14 @@ struct Layout {
     pv::QtGeom q;        // quadtree topology: node levels (n_levels = 0 for the grid)
     size_t node_bytes;   // one node-state buffer
     size_t off_node[2];
+    size_t off_qt;       // quadtree: the sweep's arguments (QtArgs for cur = 0, 1) and block offsets
     size_t total;
 };
+
+// the quadtree region at off_qt: two QtArgs (room for FP64), then the three
+// kernels' block offsets {0, blocks}
+constexpr size_t kQtArgsBytes = 2 * sizeof(pv::QtArgs<double>);
+constexpr size_t kQtRegionBytes = kQtArgsBytes + 6 * sizeof(int);
 
 bool intrinsics_ok(const pixvod_intrinsics* K) {
     return K && K->width >= 2 && K->height >= 2 && K->width <= 32768 && K->height <= 32768 &&
@@ -130,6 +136,8 @@ Layout make_layout(const pixvod_intrinsics* K, const pixvod_params* p) {
             off += L.node_bytes;
         }
     }
+    L.off_qt = off;
+    if (p->topology == PIXVOD_TOPOLOGY_QUADTREE) off += align_up(kQtRegionBytes, kAlign);
     L.total = off;
     return L;
 }
@@ -379,22 +387,53 @@ pv::QtArgs<T> qt_args(pixvod_handle* h) {
     return a;
 }
 
+// blocks of 128 threads of k_qt_node_msgs: one thread per pixel (tile order),
+// per child slot of the nodes of levels >= 2 (each slot's run padded to a warp),
+// and per node's parent slot
+unsigned qt_msg_blocks(const pixvod_handle* h) {
+    const pv::QtGeom& q = h->L.q;
+    const size_t n_px = (size_t)h->L.tiles_x * h->L.tiles_y * pv::TILE_PX;
+    const size_t n_up = q.n_levels > 1 ? (size_t)(q.n_nodes - q.base[1]) : 0;
+    const size_t threads = n_px + 4 * ((n_up + 31) / 32 * 32) + (size_t)q.n_nodes;
+    return (unsigned)((threads + 127) / 128);
+}
+
+// a quadtree handle's sweep arguments in its workspace, for cur = 0 and 1, and
+// the three kernels' block offsets {0, blocks}: a batch of one sequence, so that
+// a handle and a batch run the same kernels. Written once (pointers into the
+// workspace, geometry, factor weights).
+template <typename T>
+pixvod_status upload_qt_handle(pixvod_handle* h) {
+    pv::QtArgs<T> args[2];
+    const int keep = h->cur;
+    for (int c = 0; c < 2; ++c) {
+        h->cur = c;
+        args[c] = qt_args<T>(h);
+    }
+    h->cur = keep;
+    const dim3 pg = pixel_grid(h);
+    const int off[6] = {0, (int)(pg.x * pg.y), 0, (int)qt_msg_blocks(h), 0, (h->L.q.n_nodes + 127) / 128};
+    pixvod_status s = cuda_status(
+        cudaMemcpyAsync(h->ws + h->L.off_qt, args, sizeof(args), cudaMemcpyHostToDevice, h->stream));
+    if (s == PIXVOD_OK)
+        s = cuda_status(cudaMemcpyAsync(h->ws + h->L.off_qt + kQtArgsBytes, off, sizeof(off), cudaMemcpyHostToDevice,
+                                        h->stream));
+    if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(h->stream));  // the host copies go out of scope
+    return s;
+}
+
 // one synchronous sweep of a quadtree handle: pixels and all node levels
 template <typename T>
 pixvod_status launch_qt_sweep(pixvod_handle* h) {
-    const pv::QtArgs<T> a = qt_args<T>(h);
-    pv::k_qt_pixels<T><<<pixel_grid(h), pixel_block(), 0, h->stream>>>(a);
+    const pv::QtArgs<T>* A = reinterpret_cast<const pv::QtArgs<T>*>(h->ws + h->L.off_qt) + h->cur;
+    const int* off = reinterpret_cast<const int*>(h->ws + h->L.off_qt + kQtArgsBytes);
+    const dim3 pg = pixel_grid(h);
+    pv::k_qt_pixels<T><<<pg.x * pg.y, pixel_block(), 0, h->stream>>>(A, off, 1);
     pixvod_status s = launched(h);
     if (s != PIXVOD_OK) return s;
-    {
-        const pv::QtGeom& q = h->L.q;
-        const size_t n_px = (size_t)h->L.tiles_x * h->L.tiles_y * pv::TILE_PX;
-        const size_t n_up = q.n_levels > 1 ? (size_t)(q.n_nodes - q.base[1]) : 0;
-        const size_t threads = n_px + 4 * ((n_up + 31) / 32 * 32) + (size_t)q.n_nodes;
-        pv::k_qt_node_msgs<T><<<(unsigned)((threads + 127) / 128), 128, 0, h->stream>>>(a);
-    }
+    pv::k_qt_node_msgs<T><<<qt_msg_blocks(h), 128, 0, h->stream>>>(A, off + 2, 1);
     if ((s = launched(h)) != PIXVOD_OK) return s;
-    pv::k_qt_node_belief<T><<<(h->L.q.n_nodes + 127) / 128, 128, 0, h->stream>>>(a);
+    pv::k_qt_node_belief<T><<<(h->L.q.n_nodes + 127) / 128, 128, 0, h->stream>>>(A, off + 4, 1);
     return launched(h);
 }
 
@@ -773,6 +812,8 @@ pixvod_status pixvod_create(const pixvod_intrinsics* K, const pixvod_params* p, 
         if (s == PIXVOD_OK)
             s = cuda_status(cudaMemcpyAsync(sc->T_cur, eye, sizeof(eye), cudaMemcpyHostToDevice, h->stream));
         if (s == PIXVOD_OK) s = upload_desc(h);
+        if (s == PIXVOD_OK && is_quadtree(h))
+            s = p->precision == 64 ? upload_qt_handle<double>(h) : upload_qt_handle<float>(h);
         if (s == PIXVOD_OK) s = poison_outside(h);
         if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(h->stream));
     }
@@ -1108,6 +1149,12 @@ struct pixvod_batch {
     std::vector<const float*> frames, normals;
     int64_t frame_index;
     int64_t launches;
+    // quadtree sequences: the batched sweep's arguments (QtArgs<T> of every
+    // sequence for cur = 0, then for cur = 1) and, per kernel (pixels, node
+    // messages, node beliefs), the prefix sums of blocks per sequence
+    bool qt;
+    size_t off_qtargs, off_qtoff;
+    int qt_blocks[3];
 };
 
 namespace {
@@ -1115,7 +1162,7 @@ namespace {
 struct BatchLayout {
     std::vector<Layout> seq;
     std::vector<size_t> off_seq;
-    size_t off_desc, off_work, off_sync, total;
+    size_t off_desc, off_work, off_sync, off_qtargs, off_qtoff, total;
     int n_work;
 };
 
@@ -1135,6 +1182,12 @@ BatchLayout make_batch_layout(int n, const pixvod_intrinsics* K, const pixvod_pa
     off += align_up((size_t)B.n_work * sizeof(pv::Work), kAlign);
     B.off_sync = off;
     off += kAlign;
+    B.off_qtargs = B.off_qtoff = off;
+    if (p->topology == PIXVOD_TOPOLOGY_QUADTREE) {
+        off += align_up((size_t)2 * n * sizeof(pv::QtArgs<double>), kAlign);
+        B.off_qtoff = off;
+        off += align_up((size_t)3 * (n + 1) * sizeof(int), kAlign);
+    }
     B.total = off;
     return B;
 }
@@ -1162,6 +1215,51 @@ pixvod_status batch_launched(pixvod_batch* b) {
     return cuda_status(cudaGetLastError());
 }
 
+// quadtree batches: every sequence's sweep arguments for cur = 0 and cur = 1,
+// and the three kernels' prefix sums of blocks per sequence
+template <typename T>
+pixvod_status upload_qt(pixvod_batch* b) {
+    const int n = b->n;
+    std::vector<pv::QtArgs<T>> args(2 * (size_t)n);
+    std::vector<int> off(3 * (size_t)(n + 1), 0);
+    for (int i = 0; i < n; ++i) {
+        pixvod_handle* h = &b->seq[i];
+        const int keep = h->cur;
+        for (int c = 0; c < 2; ++c) {
+            h->cur = c;
+            args[(size_t)c * n + i] = qt_args<T>(h);
+        }
+        h->cur = keep;
+        const dim3 pg = pixel_grid(h);
+        off[i + 1] = off[i] + (int)(pg.x * pg.y);
+        off[(n + 1) + i + 1] = off[(n + 1) + i] + (int)qt_msg_blocks(h);
+        off[2 * (n + 1) + i + 1] = off[2 * (n + 1) + i] + (h->L.q.n_nodes + 127) / 128;
+    }
+    for (int k = 0; k < 3; ++k) b->qt_blocks[k] = off[k * (n + 1) + n];
+    pixvod_status s = cuda_status(cudaMemcpyAsync(b->ws + b->off_qtargs, args.data(), args.size() * sizeof(args[0]),
+                                                  cudaMemcpyHostToDevice, b->stream));
+    if (s == PIXVOD_OK)
+        s = cuda_status(cudaMemcpyAsync(b->ws + b->off_qtoff, off.data(), off.size() * sizeof(int),
+                                        cudaMemcpyHostToDevice, b->stream));
+    if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(b->stream));  // the host arrays go out of scope
+    return s;
+}
+
+// one synchronous sweep of every quadtree sequence: three launches
+template <typename T>
+pixvod_status batch_qt_sweep(pixvod_batch* b, int cur) {
+    const pv::QtArgs<T>* A = reinterpret_cast<const pv::QtArgs<T>*>(b->ws + b->off_qtargs) + (size_t)cur * b->n;
+    const int* off = reinterpret_cast<const int*>(b->ws + b->off_qtoff);
+    const int n = b->n;
+    pv::k_qt_pixels<T><<<b->qt_blocks[0], pixel_block(), 0, b->stream>>>(A, off, n);
+    pixvod_status s = batch_launched(b);
+    if (s != PIXVOD_OK) return s;
+    pv::k_qt_node_msgs<T><<<b->qt_blocks[1], 128, 0, b->stream>>>(A, off + (n + 1), n);
+    if ((s = batch_launched(b)) != PIXVOD_OK) return s;
+    pv::k_qt_node_belief<T><<<b->qt_blocks[2], 128, 0, b->stream>>>(A, off + 2 * (n + 1), n);
+    return batch_launched(b);
+}
+
 
 // sweeps of all sequences under the batch's (non-plain) schedule; every
 // sequence's `cur` advances together
@@ -1171,7 +1269,12 @@ pixvod_status batch_sweeps(pixvod_batch* b, int n_iters, int schedule) {
     pixvod_status s = cuda_status(sweep_attributes<T>());
     if (s != PIXVOD_OK) return s;
     int cur = b->seq[0].cur;
-    if (schedule == PIXVOD_SCHED_BATCHED) {
+    if (b->qt) {  // quadtree sequences: the batched schedule only
+        for (int it = 0; it < n_iters; ++it) {
+            if ((s = batch_qt_sweep<T>(b, cur)) != PIXVOD_OK) return s;
+            cur ^= 1;
+        }
+    } else if (schedule == PIXVOD_SCHED_BATCHED) {
         for (int it = 0; it < n_iters; ++it) {
             pv::k_sweeps<T><<<b->n_work, sweep_block(), pv::sweep_smem_bytes<T>(), b->stream>>>(
                 descs<T>(b), works(b), b->n_work, 1, cur, pv::GridSync{nullptr, nullptr, nullptr, 0});
@@ -1207,7 +1310,14 @@ pixvod_status batch_sweeps(pixvod_batch* b, int n_iters, int schedule) {
 template <typename T>
 pixvod_status batch_keyframe(pixvod_batch* b) {
     pv::k_batch_keyframe<T><<<b->n_work, pixel_block(), 0, b->stream>>>(descs<T>(b), works(b), b->seq[0].cur);
-    return batch_launched(b);
+    pixvod_status s = batch_launched(b);
+    for (int i = 0; i < b->n && b->qt && s == PIXVOD_OK; ++i) {  // and every node of a quadtree sequence
+        pixvod_handle* h = &b->seq[i];
+        pv::k_qt_reset<T><<<(h->L.q.n_nodes + 127) / 128, 128, 0, b->stream>>>(h->L.q, factors<T>(h).lam_P,
+                                                                                node_ptr<T>(h, h->cur));
+        s = batch_launched(b);
+    }
+    return s;
 }
 
 template <typename T>
@@ -1316,7 +1426,7 @@ extern "C" {
 pixvod_status pixvod_batch_workspace_bytes(int32_t n, const pixvod_intrinsics* K, const pixvod_params* p,
                                            size_t* out_bytes) {
     if (n < 1 || !K || !params_ok(p) || !out_bytes) return PIXVOD_EINVAL;
-    if (p->topology != PIXVOD_TOPOLOGY_GRID) return PIXVOD_EINVAL;  // batches run grid sequences
+    if (p->topology != PIXVOD_TOPOLOGY_GRID && p->topology != PIXVOD_TOPOLOGY_QUADTREE) return PIXVOD_EINVAL;
     for (int i = 0; i < n; ++i)
         if (!intrinsics_ok(&K[i])) return PIXVOD_EINVAL;
     *out_bytes = make_batch_layout(n, K, p).total;
@@ -1342,6 +1452,10 @@ pixvod_status pixvod_batch_create(int32_t n, const pixvod_intrinsics* K, const p
     b->off_desc = B.off_desc;
     b->off_work = B.off_work;
     b->off_sync = B.off_sync;
+    b->off_qtargs = B.off_qtargs;
+    b->off_qtoff = B.off_qtoff;
+    b->qt = p->topology == PIXVOD_TOPOLOGY_QUADTREE;
+    b->qt_blocks[0] = b->qt_blocks[1] = b->qt_blocks[2] = 0;
     b->n_work = B.n_work;
     b->schedule = PIXVOD_SCHED_PERSISTENT;
     b->wait_limit = pv::GRID_SYNC_DEFAULT_LIMIT;
@@ -1390,7 +1504,9 @@ pixvod_status pixvod_batch_create(int32_t n, const pixvod_intrinsics* K, const p
                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, pv::k_sweeps<float>,
                                                                             pv::SWEEP_THREADS,
                                                                             pv::sweep_smem_bytes<float>()));
-        b->max_blocks_per_sm = coop ? (m < 4 ? m : 4) : 0;
+        // the persistent schedule runs grid sequences (a quadtree sweep is three
+        // dependent launches)
+        b->max_blocks_per_sm = coop && !b->qt ? (m < 4 ? m : 4) : 0;
         b->blocks_per_sm = b->max_blocks_per_sm;
         if (b->max_blocks_per_sm < 1) b->schedule = PIXVOD_SCHED_BATCHED;
     }
@@ -1402,6 +1518,8 @@ pixvod_status pixvod_batch_create(int32_t n, const pixvod_intrinsics* K, const p
         if (s == PIXVOD_OK)
             s = cuda_status(cudaMemcpyAsync(sc->T_cur, eye, sizeof(eye), cudaMemcpyHostToDevice, b->stream));
         if (s == PIXVOD_OK) s = upload_desc(&b->seq[i]);  // for the plain schedule
+        if (s == PIXVOD_OK && b->qt)
+            s = p->precision == 64 ? upload_qt_handle<double>(&b->seq[i]) : upload_qt_handle<float>(&b->seq[i]);
         if (s == PIXVOD_OK) s = poison_outside(&b->seq[i]);
         if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(b->stream));  // eye outlives the copies
     }
@@ -1413,6 +1531,7 @@ pixvod_status pixvod_batch_create(int32_t n, const pixvod_intrinsics* K, const p
         s = cuda_status(cudaMemcpyAsync(b->ws + b->off_work, w.data(), w.size() * sizeof(pv::Work),
                                         cudaMemcpyHostToDevice, b->stream));
         if (s == PIXVOD_OK) s = p->precision == 64 ? upload_descs<double>(b) : upload_descs<float>(b);
+        if (s == PIXVOD_OK && b->qt) s = p->precision == 64 ? upload_qt<double>(b) : upload_qt<float>(b);
         if (s == PIXVOD_OK) s = cuda_status(cudaStreamSynchronize(b->stream));
     }
     if (s != PIXVOD_OK) {

@@ -115,10 +115,11 @@ __device__ __forceinline__ void identity_residual(const T* R, const T* t, const 
 // from the four grid neighbours, photometric factor, structured belief solve,
 // mu (+) tau, projected stores), with the identity message coming only from the
 // pixel's level-1 node.
+// (bx, by: the block's position in the pixel grid of blocks of 32 x 4)
 template <typename T>
-__global__ void __launch_bounds__(128) k_qt_pixels(const QtArgs<T> a) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void qt_pixels(const QtArgs<T>& a, int bx, int by) {
+    const int u = bx * blockDim.x + threadIdx.x;
+    const int v = by * blockDim.y + threadIdx.y;
     const Geometry<T>& g = a.g;
     const Factors<T>& F = a.f;
     if (u >= g.W || v >= g.H) return;
@@ -377,12 +378,12 @@ __device__ __forceinline__ T level_scale(int lvl) {
 // then the child slots of the nodes of levels >= 2 (slot-major), then the parent
 // slot of every node. Each thread issues all its loads before any arithmetic.
 template <typename T>
-__global__ void __launch_bounds__(128, 4) k_qt_node_msgs(const QtArgs<T> a) {
+__device__ __forceinline__ void qt_node_msgs(const QtArgs<T>& a, int blk) {
     const QtGeom& q = a.q;
     const Geometry<T>& g = a.g;
     const Factors<T>& F = a.f;
     const size_t st = q.stride;
-    const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t gid = (size_t)blk * blockDim.x + threadIdx.x;
     const int tiles_y = (g.H + TILE_H - 1) / TILE_H;
     const size_t n_px = (size_t)g.tiles_x * tiles_y * TILE_PX;
     const int n_up = q.n_levels > 1 ? q.n_nodes - q.base[1] : 0;     // nodes of levels >= 2
@@ -499,9 +500,9 @@ __global__ void __launch_bounds__(128, 4) k_qt_node_msgs(const QtArgs<T> a) {
 // messages k_qt_node_msgs left in the output slots (summed in slot order), belief
 // solve, Exp/Log update, and eta <- eta - Lambda tau on every slot in place.
 template <typename T>
-__global__ void __launch_bounds__(128) k_qt_node_belief(const QtArgs<T> a) {
+__device__ __forceinline__ void qt_node_belief(const QtArgs<T>& a, int blk) {
     const QtGeom& q = a.q;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blk * blockDim.x + threadIdx.x;
     if (n >= q.n_nodes) return;
     const Factors<T>& F = a.f;
     const size_t st = q.stride;
@@ -572,6 +573,48 @@ __global__ void __launch_bounds__(128) k_qt_node_belief(const QtArgs<T> a) {
         }
     }
     if (flags) atomicOr(&a.sc->flags, flags);
+}
+
+// The kernels, for one sequence or the n sequences of a batch alike (the same
+// code, so that a batch reproduces its sequences bit for bit): one launch of
+// each per sweep. Block b belongs to sequence i with off[i] <= b < off[i + 1]
+// (A[i]: its arguments in device memory, off: the kernel's prefix sums of blocks
+// per sequence, n + 1 values) and runs as block b - off[i] of that sequence's
+// grid.
+__device__ __forceinline__ int batch_seq(const int* __restrict__ off, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (__ldg(off + mid) <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k_qt_pixels(const QtArgs<T>* __restrict__ A,
+                                                         const int* __restrict__ off, int n) {
+    const int i = batch_seq(off, n, blockIdx.x);
+    const QtArgs<T>& a = A[i];
+    const int lb = blockIdx.x - __ldg(off + i);
+    const int gx = (a.g.W + (int)blockDim.x - 1) / (int)blockDim.x;
+    qt_pixels(a, lb % gx, lb / gx);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128, 4) k_qt_node_msgs(const QtArgs<T>* __restrict__ A,
+                                                               const int* __restrict__ off, int n) {
+    const int i = batch_seq(off, n, blockIdx.x);
+    qt_node_msgs(A[i], blockIdx.x - __ldg(off + i));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_qt_node_belief(const QtArgs<T>* __restrict__ A,
+                                                              const int* __restrict__ off, int n) {
+    const int i = batch_seq(off, n, blockIdx.x);
+    qt_node_belief(A[i], blockIdx.x - __ldg(off + i));
 }
 
 // Keyframe reset of every node: identity pose, belief = the level's pose prior,

@@ -210,6 +210,69 @@ def test_quadtree_refusals():
     need = ctypes.c_size_t(0)
     p = pv.params(topology=pv.TOPOLOGY_QUADTREE)
     assert pv.lib.pixvod_batch_workspace_bytes(1, ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(p),
-                                               ctypes.byref(need)) == pv.EINVAL
+                                               ctypes.byref(need)) == pv.OK  # batches take quadtree sequences
     bad = pv.params(topology=2)
     assert pv.lib.pixvod_workspace_bytes(ctypes.byref(K), ctypes.byref(bad), ctypes.byref(need)) == pv.EINVAL
+
+
+# Batches of quadtree sequences (different image sizes, keyframes): the plain
+# schedule and the batched one (one launch of each quadtree kernel per sweep for
+# all sequences) reproduce every sequence tracked alone bit for bit; the single
+# quadtree handle is checked against the oracle above. The persistent schedule
+# is refused (a quadtree sweep is three dependent launches).
+QT_SIZES = [(70, 45), (64, 48), (33, 17), (96, 64)]
+QT_FRAMES, QT_SWEEPS, QT_KF = 4, 3, 3
+
+
+def qt_batch_params(prec):
+    return pv.params(precision=prec, kf_interval=QT_KF, sigma_P=0.05, topology=pv.TOPOLOGY_QUADTREE)
+
+
+@pytest.fixture(scope="module")
+def qt_seqs():
+    out = []
+    for i, (w, h) in enumerate(QT_SIZES):
+        s = synth.realistic(60 + i, QT_FRAMES, w, h)
+        out.append((s, [torch.from_numpy(s.frame(k)).to(DEV) for k in range(QT_FRAMES)],
+                    [torch.from_numpy(s.normals(k)).to(DEV) for k in range(QT_FRAMES)]))
+    return out
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_quadtree_batch_matches_sequences_tracked_alone_bitwise(qt_seqs, prec):
+    ref_blobs, ref_poses = [], []
+    for s, frames, normals in qt_seqs:
+        trk = pv.Tracker(s.cam.as_tuple(), qt_batch_params(prec), DEV)
+        for k in range(QT_FRAMES):
+            trk.track(frames[k], normals[k] if k % QT_KF == 0 else None, n_iters=QT_SWEEPS)
+        ref_blobs.append(trk.save_state())
+        ref_poses.append(trk.pose())
+    for sched in (pv.SCHED_PLAIN, pv.SCHED_BATCHED):
+        b = pv.Batch([s.cam.as_tuple() for s, _, _ in qt_seqs], qt_batch_params(prec), DEV)
+        assert b.schedule()[0] == pv.SCHED_BATCHED  # the default for quadtree sequences
+        b.set_schedule(sched)
+        with pytest.raises(pv.PixvodError):
+            b.set_schedule(pv.SCHED_PERSISTENT, 2)
+        for k in range(QT_FRAMES):
+            b.set_inputs([f[k] for _, f, _ in qt_seqs], [n[k] for _, _, n in qt_seqs])
+            b.track(QT_SWEEPS)
+        assert b.status() == 0
+        for i in range(len(qt_seqs)):
+            assert b.save_state(i) == ref_blobs[i], (pv.SCHED_NAMES[sched], i)
+        assert np.array_equal(b.poses(), np.stack(ref_poses))
+
+
+def test_quadtree_batch_autotune_keeps_results(qt_seqs):
+    ref = pv.Batch([s.cam.as_tuple() for s, _, _ in qt_seqs], qt_batch_params(32), DEV)
+    tuned = pv.Batch([s.cam.as_tuple() for s, _, _ in qt_seqs], qt_batch_params(32), DEV)
+    for k in range(QT_FRAMES):
+        for b in (ref, tuned):
+            b.set_inputs([f[k] for _, f, _ in qt_seqs], [n[k] for _, _, n in qt_seqs])
+            b.track(QT_SWEEPS)
+        if k == 0:
+            times, (sched, _) = tuned.autotune(QT_SWEEPS, 1)
+            assert times["plain"] > 0 and times["batched"] > 0
+            assert times["persistent2"] < 0 and times["persistent4"] < 0  # not candidates
+            assert sched in (pv.SCHED_PLAIN, pv.SCHED_BATCHED)
+    for i in range(len(qt_seqs)):
+        assert tuned.save_state(i) == ref.save_state(i), i
