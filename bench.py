@@ -671,17 +671,19 @@ def run_batched(args):
     px = sum(q.cam.width * q.cam.height for q in fam)
     params = pv.params(precision=32, kf_interval=10, sigma_P=fam[0].sigma_P)
     stream = torch.cuda.Stream(dev)
-    results = {}
-    for mode in ("tuned", "plain"):
+
+    def timed(prm, mode):
+        """The timed steps of one batch: mode "tuned" (autotuner after the first
+        keyframe), "plain" or "batched" (that schedule)."""
         with torch.cuda.stream(stream):
-            b = pv.Batch(Ks, params, dev, stream=stream)
+            b = pv.Batch(Ks, prm, dev, stream=stream)
             b.set_inputs([frames[i][0] for i in range(64)], [normals[i][0] for i in range(64)])
             b.track(args.sweeps)
             tune = None
             if mode == "tuned":
                 tune = b.autotune(args.sweeps, 2)
             else:
-                b.set_schedule(pv.SCHED_PLAIN)
+                b.set_schedule(pv.SCHED_PLAIN if mode == "plain" else pv.SCHED_BATCHED)
             for k in range(1, 1 + args.warmup):
                 b.set_inputs([frames[i][k] for i in range(64)], [normals[i][k] for i in range(64)])
                 b.track(args.sweeps)
@@ -695,11 +697,18 @@ def run_batched(args):
             ev1.record(stream)
             ev1.synchronize()
             ms = ev0.elapsed_time(ev1)
-            results[mode] = {"ms": ms, "value": px * args.sweeps * args.steps / (ms * 1e-3) / 1e6,
-                             "launches": b.launch_count() - n0, "schedule": b.schedule(), "tune": tune,
-                             "flags": b.status(), "poses": b.poses()}
+            out = {"ms": ms, "value": px * args.sweeps * args.steps / (ms * 1e-3) / 1e6,
+                   "launches": b.launch_count() - n0, "schedule": b.schedule(), "tune": tune,
+                   "flags": b.status(), "poses": b.poses()}
             del b
+            return out
+
+    results = {mode: timed(params, mode) for mode in ("tuned", "plain")}
     same = bool(np.array_equal(results["tuned"]["poses"], results["plain"]["poses"]))
+    # the same sequences with the quadtree identity topology: one launch of each
+    # quadtree kernel per sweep for all 64 against every sequence's own launches
+    qparams = pv.params(precision=32, kf_interval=10, sigma_P=fam[0].sigma_P, topology=pv.TOPOLOGY_QUADTREE)
+    qt = {mode: timed(qparams, mode) for mode in ("batched", "plain")}
     # the persistent schedule (4 blocks per SM) replayed from a captured CUDA graph,
     # against the same schedule launched eagerly: no re-anchoring here (a captured
     # step is one kind of frame step), frames copied into the registered buffers
@@ -767,8 +776,16 @@ def run_batched(args):
             "graph_replay": {k: graph["graph"][k] for k in ("value", "ms_per_step")},
             "eager": {k: graph["eager"][k] for k in ("value", "ms_per_step")},
             "identical_poses": bool(np.array_equal(graph["graph"]["poses"], graph["eager"]["poses"]))},
+        "quadtree": {
+            "note": "the same 64 sequences with the quadtree identity topology",
+            "batched": {"value": qt["batched"]["value"], "ms_per_step": qt["batched"]["ms"] / args.steps,
+                        "launches": qt["batched"]["launches"]},
+            "plain": {"value": qt["plain"]["value"], "ms_per_step": qt["plain"]["ms"] / args.steps,
+                      "launches": qt["plain"]["launches"]},
+            "speedup_vs_plain": qt["batched"]["value"] / qt["plain"]["value"],
+            "identical_poses": bool(np.array_equal(qt["batched"]["poses"], qt["plain"]["poses"]))},
         "device_flags": results["tuned"]["flags"] | results["plain"]["flags"] | graph["graph"]["flags"]
-                        | graph["eager"]["flags"],
+                        | graph["eager"]["flags"] | qt["batched"]["flags"] | qt["plain"]["flags"],
     }
     print(json.dumps(line), flush=True)
     return 0
