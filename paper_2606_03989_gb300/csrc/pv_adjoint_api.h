@@ -61,10 +61,11 @@ struct AdjArgs {
 cudaError_t launch_adjoint_sweep(const AdjArgs& A, int blocks, cudaStream_t st);
 // adjoint of one sweep by the hand-written reverse pass, in the state's
 // precision, as ADJOINT_HW_LAUNCHES launches: per pixel and direction (the
-// damped identity messages, forward), per pixel (the update and the reverse pass
-// of everything but the identity messages), per pixel (the recompute check), per
-// pixel and direction (the identity messages' reverse pass), per pixel (the
-// pose); `scratch` (adjoint_scratch_bytes) carries values between them
+// damped identity messages and what their reverse needs, summed over the
+// directions), per pixel (the update and the reverse pass of everything but the
+// identity messages), per pixel and direction (the identity messages' reverse
+// pass), per tile (the recompute check), per pixel (the pose); `scratch`
+// (adjoint_scratch_bytes) carries values between them
 constexpr int ADJOINT_HW_LAUNCHES = 5;
 size_t adjoint_scratch_bytes(int n_tiles, int state64);
 cudaError_t launch_adjoint_hw(const AdjArgs& A, int n_tiles, void* scratch, cudaStream_t st);
