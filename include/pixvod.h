@@ -300,19 +300,20 @@ pixvod_status pixvod_set_recording(pixvod_handle* h, void* d_workspace, size_t w
  * frame intensities) (width*height row-major each). check (host, optional,
  * 2 doubles): the largest difference between the reverse pass's own
  * recomputation of a pixel update and the sweep kernel's result, relative to
- * the magnitude of the output (at least 1; for the hand-written pass, the
- * projected messages eta - Lambda tau are measured against |eta| + |Lambda tau|,
- * whose rounding they carry), and (tape pass) the longest tape. Synchronises
- * the stream.
+ * the magnitude of the output (at least 1; for the hand-written pass, also
+ * against its block's scale, that of a 6 x 6 solve's rounding: sqrt(|A_rr A_cc|)
+ * for entry (r, c) of M_p or of a message's Lambda, the largest stored entry for
+ * an entry of xi, u or a message's eta; and the projected messages
+ * eta - Lambda tau against |eta| + |Lambda tau|, whose rounding they carry), and
+ * (tape pass) the longest tape. Synchronises the stream.
  * ESTATE if recording is off or the last call was not a non-anchoring target
  * frame tracked with recording on; ENUMERIC if a pixel's tape overflowed, or if
  * that recomputation differs by more than PIXVOD_RECOMPUTE_TOL_FP32 (FP32
  * arithmetic) or PIXVOD_RECOMPUTE_TOL_FP64 (FP64): the gradients then belong to
  * a different update than the one the forward ran. In FP64 the recomputation
- * is exact to rounding; in FP32 two evaluations of the same update differ by
- * rounding that the belief solve's conditioning amplifies (measured up to
- * about 1e-2 at 320x240), so the FP32 bound only catches gross differences. */
-#define PIXVOD_RECOMPUTE_TOL_FP32 1e-1
+ * is exact to rounding (about 1e-12 at 320x240); in FP32 two evaluations of the
+ * same update differ by rounding (measured up to about 1e-3 at 320x240). */
+#define PIXVOD_RECOMPUTE_TOL_FP32 1e-2
 #define PIXVOD_RECOMPUTE_TOL_FP64 1e-9
 pixvod_status pixvod_backward(pixvod_handle* h, const double* d_grad_xi, const double* d_grad_invdepth,
                               double* d_grad_sigmas, double* d_grad_Is, double* d_grad_It, double* check);

@@ -382,11 +382,14 @@ __global__ void __launch_bounds__(TILE_PX, sizeof(T) == 4 ? 4 : 1) k_adjoint_dir
 // here from SCR_FWD and tau as the update forms it (Lambda' = Lambda, eta' =
 // eta - Lambda tau, zero without a neighbour). The outputs of a group are known
 // at compile time, so each thread's loads are issued together. Each output is
-// compared with the sweep kernel's relative to max(|stored|, the magnitude of
-// the terms it is formed from); the largest difference goes to A.mismatch (one
-// atomic per block).
-// (divides only when the maximum grows: |y - r| > mm den decides it; a NaN
-// difference never does)
+// compared with the sweep kernel's relative to the largest of |stored|, 1, the
+// magnitude of the terms it is formed from, and its block's scale, the scale of
+// a 6 x 6 solve's rounding: sqrt(|A_rr A_cc|) for entry (r, c) of a symmetric
+// positive semidefinite block (M_p, a message's Lambda), the largest stored
+// entry for an entry of a 6-vector (xi, u, a message's eta). The largest
+// difference goes to A.mismatch (one atomic per block).
+// (check_value divides only when the maximum grows: |y - r| > mm den decides
+// it; a NaN difference never does)
 template <typename T>
 __device__ __forceinline__ void check_value(T yq, T s, T rq, T& mm) {
     const T den = v_abs(rq) > s ? v_abs(rq) : s;
@@ -395,6 +398,11 @@ __device__ __forceinline__ void check_value(T yq, T s, T rq, T& mm) {
         const T e = d / den;
         mm = e > mm ? e : mm;
     }
+}
+
+template <typename T>
+__device__ __forceinline__ T unit_scale(T y) {
+    return v_abs(y) > T(1) ? v_abs(y) : T(1);
 }
 
 __device__ __forceinline__ void ld16(const float* p, float* o) {
@@ -410,16 +418,71 @@ __device__ __forceinline__ void ld16(const double* p, double* o) {
     o[1] = x.y;
 }
 
-// one output of the main stage: recomputed values y, stored ref (NV lanes)
+// a symmetric 6 x 6 block (packed planes of the recomputed y and the stored
+// ref, lane-offset pointers to the block's first plane); zero[j]: the block is
+// zero in lane j (no neighbour)
 template <typename T, int NV>
-__device__ __forceinline__ void check_main_output(const T* sp, const T* ref, int q, int nval, T& mm) {
+__device__ __forceinline__ void check_sym(const T* y, const T* ref, int nval, const bool* zero, T& mm) {
+#pragma unroll 1
+    for (int r = 0; r < 6; ++r) {  // row by row: a row's loads in flight together
+        T dr[NV];
+        ld16(ref + pidx(r, r) * TILE_PX, dr);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            if (c > r) break;
+            T yv[NV], rv[NV], dc[NV];
+            ld16(y + pidx(r, c) * TILE_PX, yv);
+            ld16(ref + pidx(r, c) * TILE_PX, rv);
+            ld16(ref + pidx(c, c) * TILE_PX, dc);
+            for (int j = 0; j < NV; ++j) {
+                const T yj = zero[j] ? T(0) : yv[j];
+                const T b = v_sqrt(v_abs(dr[j])) * v_sqrt(v_abs(dc[j])), u = unit_scale(yj);
+                if (j < nval) check_value(yj, b > u ? b : u, rv[j], mm);
+            }
+        }
+    }
+}
+
+// the scale of a 6-vector block: its largest stored entry (6 planes from ref)
+template <typename T, int NV>
+__device__ __forceinline__ void vec_scale(const T* ref, T* b) {
+    for (int j = 0; j < NV; ++j) b[j] = T(0);
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        T rv[NV];
+        ld16(ref + r * TILE_PX, rv);
+        for (int j = 0; j < NV; ++j) b[j] = v_abs(rv[j]) > b[j] ? v_abs(rv[j]) : b[j];
+    }
+}
+
+// a vector block the main stage wrote (SCR_CHK planes q0.., unit scales)
+template <typename T, int NV>
+__device__ __forceinline__ void check_main_vec(const T* sp, const T* ref, int q0, int nval, T& mm) {
+    T b[NV];
+    vec_scale<T, NV>(ref + q0 * TILE_PX, b);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        T y[NV], r[NV];
+        ld16(sp + (SCR_CHK + chk_plane(q0 + q)) * TILE_PX, y);
+        ld16(ref + (q0 + q) * TILE_PX, r);
+        for (int j = 0; j < NV; ++j) {
+            const T u = unit_scale(y[j]);
+            if (j < nval) check_value(y[j], u > b[j] ? u : b[j], r[j], mm);
+        }
+    }
+}
+
+// a scalar output the main stage wrote; with sp_scale, its stored scale plane
+template <typename T, int NV>
+__device__ __forceinline__ void check_main_scalar(const T* sp, const T* ref, int q, const T* sp_scale, int nval,
+                                                  T& mm) {
     T y[NV], r[NV], sc[NV];
     ld16(sp + (SCR_CHK + chk_plane(q)) * TILE_PX, y);
     ld16(ref + q * TILE_PX, r);
-    if (q >= 144 && (q & 1) == 0)
-        ld16(sp + (SCR_CHK_S + (q - 144) / 2) * TILE_PX, sc);
+    if (sp_scale)
+        ld16(sp_scale, sc);
     else
-        for (int j = 0; j < NV; ++j) sc[j] = v_abs(y[j]) > T(1) ? v_abs(y[j]) : T(1);
+        for (int j = 0; j < NV; ++j) sc[j] = unit_scale(y[j]);
     for (int j = 0; j < NV; ++j)
         if (j < nval) check_value(y[j], sc[j], r[j], mm);
 }
@@ -439,33 +502,32 @@ __global__ void __launch_bounds__(5 * TILE_PX / (16 / sizeof(T))) k_adjoint_chec
         const T* sp = scr + (size_t)tile * SCR_WORDS + lane0;
         const T* ref = static_cast<const T*>(A.state_out) + (size_t)tile * TILE_WORDS + lane0;
         if (grp == 0) {
+            const bool none[NV] = {};
+            check_main_vec<T, NV>(sp, ref, 0, nval, mm);                // xi
+            check_main_scalar<T, NV>(sp, ref, 6, nullptr, nval, mm);    // log-depth
+            check_sym<T, NV>(sp + (SCR_CHK + chk_plane(7)) * TILE_PX, ref + 7 * TILE_PX, nval, none, mm);  // M_p
+            check_main_vec<T, NV>(sp, ref, 28, nval, mm);               // u
+            check_main_scalar<T, NV>(sp, ref, 34, nullptr, nval, mm);   // s
 #pragma unroll
-            for (int q = 0; q < 35; ++q) check_main_output<T, NV>(sp, ref, q, nval, mm);
-#pragma unroll
-            for (int q = 143; q < hw::N_OUT; ++q) check_main_output<T, NV>(sp, ref, q, nval, mm);
+            for (int k = 0; k < 4; ++k) {  // normal messages: Lambda, eta (its terms' scale stored)
+                check_main_scalar<T, NV>(sp, ref, 143 + 2 * k, nullptr, nval, mm);
+                check_main_scalar<T, NV>(sp, ref, 144 + 2 * k, sp + (SCR_CHK_S + k) * TILE_PX, nval, mm);
+            }
         } else {
             const int k = grp - 1;
-            bool has[NV];
+            bool none[NV];
             for (int j = 0; j < NV; ++j) {
                 const int u = u0 + j;
-                has[j] = k == 0 ? u > 0 : (k == 1 ? u + 1 < g.W : (k == 2 ? v > 0 : v + 1 < g.H));
+                none[j] = !(k == 0 ? u > 0 : (k == 1 ? u + 1 < g.W : (k == 2 ? v > 0 : v + 1 < g.H)));
             }
             const T* Lk = sp + (SCR_FWD + 27 * k) * TILE_PX;
             const T* rk = ref + (35 + 27 * k) * TILE_PX;
-#pragma unroll
-            for (int p = 0; p < 21; ++p) {
-                T y[NV], r[NV];
-                ld16(Lk + p * TILE_PX, y);
-                ld16(rk + p * TILE_PX, r);
-                for (int j = 0; j < NV; ++j) {
-                    const T yj = has[j] ? y[j] : T(0);
-                    if (j < nval) check_value(yj, v_abs(yj) > T(1) ? v_abs(yj) : T(1), r[j], mm);
-                }
-            }
-            T tau[6][NV];
+            check_sym<T, NV>(Lk, rk, nval, none, mm);  // Lambda' = Lambda
+            T tau[6][NV], b[NV];
             for (int cc = 0; cc < 6; ++cc) ld16(sp + (SCR_MAIN + hw::MO_TAU + cc) * TILE_PX, tau[cc]);
-#pragma unroll
-            for (int rr = 0; rr < 6; ++rr) {
+            vec_scale<T, NV>(rk + 21 * TILE_PX, b);
+#pragma unroll 1
+            for (int rr = 0; rr < 6; ++rr) {  // eta' = eta - Lambda tau, row by row
                 T Lr[6][NV], er[NV], r[NV];
                 for (int cc = 0; cc < 6; ++cc) ld16(Lk + pidx(rr, cc) * TILE_PX, Lr[cc]);
                 ld16(Lk + (21 + rr) * TILE_PX, er);
@@ -477,11 +539,11 @@ __global__ void __launch_bounds__(5 * TILE_PX / (16 / sizeof(T))) k_adjoint_chec
                         tj[cc] = tau[cc][j];
                     }
                     hw::projected_eta_row(Lrow, er[j], tj, &y, &sc);
-                    if (!has[j]) {
+                    if (none[j]) {
                         y = T(0);
                         sc = T(1);
                     }
-                    if (j < nval) check_value(y, sc, r[j], mm);
+                    if (j < nval) check_value(y, sc > b[j] ? sc : b[j], r[j], mm);
                 }
             }
         }

@@ -241,11 +241,11 @@ def test_reverse_pass_follows_the_forward_at_the_adjoint_workload_size():
     recomputation of every pixel update equals the sweep kernel's result to FP64
     rounding, so it differentiates the update that ran (no validity or Huber
     branch taken differently, which would show as an O(1) difference). FP32: the
-    same recomputation in float differs from the float sweep only by rounding,
-    which the belief solve's conditioning amplifies (about 1e-2 of the terms an
-    output is formed from); the status stays OK under the documented bound."""
+    same recomputation in float differs from the float sweep only by rounding
+    (4.6e-4 measured, each output relative to the terms it is formed from and
+    to its block's scale); the status stays OK under the documented bound."""
     seq = synth.adjoint_family(1, 2)[0]
-    for prec, tol in ((64, 1e-9), (32, 5e-2)):
+    for prec, tol in ((64, 1e-9), (32, 2e-3)):
         trk = pv.Tracker(seq.cam.as_tuple(), pv.params(precision=prec, kf_interval=0, sigma_P=seq.sigma_P), DEV)
         trk.set_recording(30, 5)
         trk.track(torch.from_numpy(seq.frame(0)).to(DEV), torch.from_numpy(seq.normals(0)).to(DEV))
