@@ -793,7 +793,8 @@ def run_batched(args):
 
 def run_adjoint(args):
     """Adjoint workload: 8 sequences of the realistic family at 320x240 (fx=fy=262.5),
-    30 sweeps per frame, checkpoints every 5 sweeps. One step = every sequence
+    30 sweeps per frame, every intermediate state kept by the forward (recording
+    with checkpoint_every = 1: the reverse pass recomputes nothing). One step = every sequence
     tracks one frame (FP32 state, recording on) and back-propagates the frame's
     loss |xi_est - xi_gt|^2 + mean_px (exp(-mu_6) - 1/z_gt)^2 through its sweeps
     (hand-written adjoint in the state's FP32), giving dL/dsigma_D, dL/dsigma_N, dL/dI_s and dL/dI_t. The same
@@ -803,7 +804,7 @@ def run_adjoint(args):
     import torch
     import paper_2606_03989_gb300 as pv
     sys.path.insert(0, ROOT)
-    n_seq, sweeps, every = 8, 30, 5
+    n_seq, sweeps, every = 8, 30, 1
     n_frames = 1 + args.warmup + args.steps
     fam = synth.adjoint_family(n_seq, n_frames)
     jobs = [(i, k, n_frames) for i in range(n_seq) for k in range(n_frames)]
@@ -869,8 +870,8 @@ def run_adjoint(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (state and hand-written adjoint)",
         "data": "synthetic",
         "config": {"workload": "adjoint: 8 sequences of the realistic family (seeds 2000-2007) at 320x240, "
-                               "fx=fy=262.5, %d sweeps per frame, checkpoint every %d sweeps, loss per frame "
-                               "truncated at the frame start" % (sweeps, every),
+                               "fx=fy=262.5, %d sweeps per frame, every intermediate state kept (checkpoint every "
+                               "%d sweep), loss per frame truncated at the frame start" % (sweeps, every),
                    "pixels_per_step": px},
         "forward_only": {"value": px * sweeps * args.steps / (fw * 1e-3) / 1e6, "ms_per_step": fw / args.steps},
         "time_ratio_fwd_bwd_over_fwd": fb / fw,

@@ -271,7 +271,12 @@ pixvod_status pixvod_launch_count(pixvod_handle* h, int64_t* out);
 
 /* Device bytes of the recording workspace for frames of at most max_iters
  * sweeps (>= 1) with a checkpoint every checkpoint_every (>= 1) sweeps, for the
- * hand-written reverse pass (no CUDA calls). */
+ * hand-written reverse pass (no CUDA calls). checkpoint_every = 1 keeps every
+ * intermediate state of the frame (max_iters - 1 states, written by the sweeps
+ * themselves, no copies) and every sweep's decisions, so that pixvod_backward
+ * recomputes nothing; larger values keep one state per checkpoint_every sweeps
+ * and pixvod_backward recomputes each segment from its checkpoint (the same
+ * bits). */
 pixvod_status pixvod_backward_workspace_bytes(const pixvod_intrinsics* K, const pixvod_params* p,
                                               int32_t max_iters, int32_t checkpoint_every, size_t* out_bytes);
 

@@ -146,11 +146,15 @@ Layout make_layout(const pixvod_intrinsics* K, const pixvod_params* p) {
 // every `every` sweeps, the states of one segment recomputed from a checkpoint
 // with each sweep's recorded decisions (a byte per pixel), two adjoint states,
 // descriptors of the recompute launches, a few accumulators and, for the tape
-// cross-check only, the reverse-mode tapes of the tape kernel.
+// cross-check only, the reverse-mode tapes of the tape kernel. With every == 1
+// (keep_all) the frame's sweeps write every intermediate state S_1 .. S_{n-1}
+// to the checkpoint slots and their decisions to one slot each, so that the
+// reverse pass recomputes nothing.
 constexpr int kTapeCap = 8192;            // tape nodes per thread (at most 7133 seen)
 constexpr int kAdjSlotsPerSM = 256;       // adjoint threads per SM (eight blocks of one warp)
 struct RecLayout {
     int n_ckpt, every, max_iters, slots;
+    bool keep_all;
     size_t state_bytes, adj_bytes, br_bytes;
     size_t off_ckpt, off_seg, off_br, off_adj[2], off_scr, off_desc, off_misc, off_par, off_w, off_tadj, total;
 };
@@ -159,7 +163,8 @@ RecLayout make_rec_layout(const Layout& L, int max_iters, int every, int n_px, i
     RecLayout R;
     R.every = every;
     R.max_iters = max_iters;
-    R.n_ckpt = (max_iters - 1) / every + 1;
+    R.keep_all = every == 1;
+    R.n_ckpt = R.keep_all ? (max_iters > 1 ? max_iters - 1 : 1) : (max_iters - 1) / every + 1;
     R.slots = tape ? num_sms * kAdjSlotsPerSM : 0;
     const int need = (n_px + pv::ad::ADJ_THREADS - 1) / pv::ad::ADJ_THREADS * pv::ad::ADJ_THREADS;
     if (need < R.slots) R.slots = need;
@@ -172,7 +177,7 @@ RecLayout make_rec_layout(const Layout& L, int max_iters, int every, int n_px, i
     R.off_seg = off;
     off += (size_t)every * R.state_bytes;
     R.off_br = off;
-    off += (size_t)every * R.br_bytes;
+    off += (size_t)(R.keep_all ? max_iters : every) * R.br_bytes;
     for (int b = 0; b < 2; ++b) {
         R.off_adj[b] = off;
         off += R.adj_bytes;
@@ -466,11 +471,51 @@ pixvod_status run_sweeps(pixvod_handle* h, int n) {
     return PIXVOD_OK;
 }
 
+// keep_all recording of an n-sweep frame whose sweeps started from state buffer
+// cur0: S_0 is that buffer, S_c (0 < c < n) checkpoint slot c - 1, S_n the other
+// state buffer (the handle's state after the frame); the decisions of sweep c
+// (1-based) in recording slot c - 1
+template <typename T>
+T* kept_state(pixvod_handle* h, int cur0, int c, int n) {
+    if (c == 0) return state_ptr<T>(h, cur0);
+    if (c == n) return state_ptr<T>(h, cur0 ^ 1);
+    return reinterpret_cast<T*>(h->rec_ws + h->RL.off_ckpt + (size_t)(c - 1) * h->RL.state_bytes);
+}
+unsigned char* kept_br(pixvod_handle* h, int c) {
+    return reinterpret_cast<unsigned char*>(h->rec_ws + h->RL.off_br + (size_t)(c - 1) * h->RL.br_bytes);
+}
+
 // the frame's sweeps with checkpoints for the adjoint: S_c before sweep c + 1
-// for c = 0, every, 2 every, ... (c < n)
+// for c = 0, every, 2 every, ... (c < n); with keep_all, every S_c
 template <typename T>
 pixvod_status run_sweeps_recorded(pixvod_handle* h, int n) {
     const RecLayout& R = h->RL;
+    if (R.keep_all) {
+        if (n <= 0) return PIXVOD_OK;
+        pixvod_status s = cuda_status(sweep_attributes<T>());
+        if (s != PIXVOD_OK) return s;
+        const int cur0 = h->cur, n_tiles = h->L.tiles_x * h->L.tiles_y;
+        std::vector<pv::SeqDesc<T>> descs(n);
+        for (int c = 1; c <= n; ++c) {  // sweep c maps S_{c-1} to S_c and records its decisions
+            pv::SeqDesc<T> d = seq_desc<T>(h, nullptr, nullptr);
+            d.state[0] = kept_state<T>(h, cur0, c - 1, n);
+            d.state[1] = kept_state<T>(h, cur0, c, n);
+            d.br = kept_br(h, c);
+            descs[c - 1] = d;
+        }
+        // pageable source: the copy is staged before the call returns
+        s = cuda_status(cudaMemcpyAsync(h->rec_ws + R.off_desc, descs.data(), (size_t)n * sizeof(pv::SeqDesc<T>),
+                                        cudaMemcpyHostToDevice, h->stream));
+        if (s != PIXVOD_OK) return s;
+        const pv::SeqDesc<T>* dd = reinterpret_cast<const pv::SeqDesc<T>*>(h->rec_ws + R.off_desc);
+        for (int c = 1; c <= n; ++c) {
+            pv::k_sweeps<T><<<n_tiles, sweep_block(), pv::sweep_smem_bytes<T>(), h->stream>>>(
+                dd + (c - 1), nullptr, n_tiles, 1, 0, pv::GridSync{nullptr, nullptr, nullptr, 0});
+            if ((s = launched(h)) != PIXVOD_OK) return s;
+        }
+        h->cur = cur0 ^ 1;
+        return PIXVOD_OK;
+    }
     for (int c = 0; c < n; c += R.every) {
         pixvod_status s = cuda_status(cudaMemcpyAsync(h->rec_ws + R.off_ckpt + (size_t)(c / R.every) * R.state_bytes,
                                                       h->ws + h->L.off_state[h->cur], R.state_bytes,
@@ -572,7 +617,7 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
     // and records its decisions in brbuf(j)
     std::vector<pv::SeqDesc<T>> descs(n > 0 ? n : 1);
     const int n_seg = (n + k - 1) / k;
-    for (int seg = 0; seg < n_seg; ++seg)
+    for (int seg = 0; seg < n_seg && !R.keep_all; ++seg)
         for (int j = 1; j <= k && seg * k + j <= n; ++j) {
             pv::SeqDesc<T> d = seq_desc<T>(h, nullptr, nullptr);
             d.state[0] = j == 1 ? ckpt(seg) : segbuf(j - 1);
@@ -580,7 +625,7 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
             d.br = brbuf(j);
             descs[seg * k + j - 1] = d;
         }
-    if (n > 0)
+    if (n > 0 && !R.keep_all)
         s = cuda_status(cudaMemcpyAsync(rw + R.off_desc, descs.data(), (size_t)n * sizeof(pv::SeqDesc<T>),
                                         cudaMemcpyHostToDevice, st));
     if (s != PIXVOD_OK) return s;
@@ -628,7 +673,40 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
     int a = 0;  // adjoint buffer holding the adjoint of the later state
     // sweeps first+1 .. n are differentiated; the state after sweep `first` is a constant
     const int first = h->rec_window > 0 && h->rec_window < n ? n - h->rec_window : 0;
-    for (int seg = n_seg - 1; seg >= 0; --seg) {
+    // the reverse pass of one sweep S_in -> S_out with its recorded decisions
+    auto reverse_sweep = [&](T* in, T* out, unsigned char* br) -> pixvod_status {
+        A.state_in = in;
+        A.state_out = out;
+        A.adj_out = adj[a];
+        A.adj_in = adj[a ^ 1];
+        A.br = br;
+        pixvod_status r = cuda_status(cudaMemsetAsync(adj[a ^ 1], 0, R.adj_bytes, st));
+        if (r != PIXVOD_OK) return r;
+        if (tape) {
+            h->launches++;
+            if ((r = cuda_status(pv::launch_adjoint_sweep(A, R.slots / pv::ad::ADJ_THREADS, st))) != PIXVOD_OK)
+                return r;
+        } else {
+            // rescale by a power of two: max |adj_out|, the pass, the new exponent
+            if ((r = cuda_status(cudaMemsetAsync(scale + 1, 0, sizeof(double), st))) != PIXVOD_OK) return r;
+            h->launches += 2 + pv::ADJOINT_HW_LAUNCHES;  // absmax, the pass, the exponent
+            if ((r = cuda_status(pv::launch_adjoint_absmax(adj[a], adj_elems, adj64 ? 1 : 0, scale, st))) !=
+                PIXVOD_OK)
+                return r;
+            if ((r = cuda_status(pv::launch_adjoint_hw(A, n_tiles, rw + R.off_scr, st))) != PIXVOD_OK) return r;
+            if ((r = cuda_status(pv::launch_adjoint_exponent(scale, st))) != PIXVOD_OK) return r;
+        }
+        a ^= 1;
+        return PIXVOD_OK;
+    };
+    if (R.keep_all) {  // every state kept by the forward: nothing to recompute
+        const int cur0 = h->cur ^ 1;
+        for (int c = n; c > first; --c)
+            if ((s = reverse_sweep(kept_state<T>(h, cur0, c - 1, n), kept_state<T>(h, cur0, c, n), kept_br(h, c))) !=
+                PIXVOD_OK)
+                return s;
+    }
+    for (int seg = n_seg - 1; seg >= 0 && !R.keep_all; --seg) {
         const int c = seg * k, len = n - c < k ? n - c : k;
         if (c + len <= first) break;
         for (int j = 1; j <= len; ++j) {
@@ -636,29 +714,8 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
                 ddesc + (c + j - 1), nullptr, n_tiles, 1, 0, pv::GridSync{nullptr, nullptr, nullptr, 0});
             if ((s = launched(h)) != PIXVOD_OK) return s;
         }
-        for (int j = len; j >= 1 && c + j > first; --j) {
-            A.state_in = j == 1 ? ckpt(seg) : segbuf(j - 1);
-            A.state_out = segbuf(j);
-            A.adj_out = adj[a];
-            A.adj_in = adj[a ^ 1];
-            A.br = brbuf(j);
-            if ((s = cuda_status(cudaMemsetAsync(adj[a ^ 1], 0, R.adj_bytes, st))) != PIXVOD_OK) return s;
-            if (tape) {
-                h->launches++;
-                if ((s = cuda_status(pv::launch_adjoint_sweep(A, R.slots / pv::ad::ADJ_THREADS, st))) != PIXVOD_OK)
-                    return s;
-            } else {
-                // rescale by a power of two: max |adj_out|, the pass, the new exponent
-                if ((s = cuda_status(cudaMemsetAsync(scale + 1, 0, sizeof(double), st))) != PIXVOD_OK) return s;
-                h->launches += 2 + pv::ADJOINT_HW_LAUNCHES;  // absmax, the pass, the exponent
-                if ((s = cuda_status(pv::launch_adjoint_absmax(adj[a], adj_elems, adj64 ? 1 : 0, scale, st))) !=
-                    PIXVOD_OK)
-                    return s;
-                if ((s = cuda_status(pv::launch_adjoint_hw(A, n_tiles, rw + R.off_scr, st))) != PIXVOD_OK) return s;
-                if ((s = cuda_status(pv::launch_adjoint_exponent(scale, st))) != PIXVOD_OK) return s;
-            }
-            a ^= 1;
-        }
+        for (int j = len; j >= 1 && c + j > first; --j)
+            if ((s = reverse_sweep(j == 1 ? ckpt(seg) : segbuf(j - 1), segbuf(j), brbuf(j))) != PIXVOD_OK) return s;
     }
     h->launches++;
     s = cuda_status(pv::launch_sigma_grads(dparam, double(h->p.sigma_D), double(h->p.sigma_N), g_sig, st));

@@ -62,10 +62,10 @@ def oracle_loss(c, I_s=None, I_t=None, **sig):
     return loss(c, xi, np.exp(-trk.state.mu[..., 6]))
 
 
-def gpu_run(c, precision=64, window=None, method=0):
+def gpu_run(c, precision=64, window=None, method=0, every=EVERY):
     seq = c["seq"]
     trk = pv.Tracker(seq.cam.as_tuple(), pv.params(precision=precision, kf_interval=0, sigma_P=seq.sigma_P), DEV)
-    trk.set_recording(SWEEPS, EVERY, method)
+    trk.set_recording(SWEEPS, every, method)
     if window is not None:
         trk.set_backward_window(window)
     trk.track(torch.from_numpy(c["I_s"]).to(DEV), torch.from_numpy(c["n"]).to(DEV))
@@ -105,6 +105,28 @@ def plateau(f, x0, unit):
 
 def assert_close(g, fd, scale):
     assert abs(g - fd) <= RTOL * max(abs(fd), scale), (g, fd, scale)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_keeping_every_state_needs_no_recomputation(case, precision, gpu64):
+    """checkpoint_every = 1: the frame's sweeps write every intermediate state
+    and every sweep's decisions, and the reverse pass recomputes nothing. The
+    tracked frame is bit-identical to the checkpointed run's (the same kernel on
+    other buffers), the recompute check sees the same states, and in FP64 the
+    gradients equal the checkpointed run's (to the order of the atomic sums)."""
+    t1, xi1, inv1, g1 = gpu_run(case, precision, every=1)
+    t5, xi5, inv5, g5 = gpu64 if precision == 64 else gpu_run(case, precision)
+    assert np.array_equal(xi1, xi5) and np.array_equal(inv1, inv5)
+    assert g1["status"] == pv.OK
+    assert g1["recompute_mismatch"] == g5["recompute_mismatch"]
+    if precision == 64:
+        for k in ("sigma_D", "sigma_N"):
+            assert float(g1[k]) == pytest.approx(float(g5[k]), rel=1e-9), k
+        for k in ("I_s", "I_t"):
+            err = float((g1[k] - g5[k]).norm() / g5[k].norm())
+            assert err < 1e-9, (k, err)
+    # the reverse pass launches no sweep kernel
+    assert t1.launch_count() < t5.launch_count()
 
 
 def test_recomputed_update_equals_the_sweep_kernel(gpu64, gpu64_tape):
