@@ -664,6 +664,7 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
     A.tape.n_slots = R.slots;
     A.scale = scale;
     const size_t adj_elems = (size_t)n_tiles * pv::TILE_WORDS;
+    const size_t adj_used = adj_elems * (adj64 ? sizeof(double) : sizeof(float));  // of the FP64-sized buffers
     // the prior mean of the segment the frame was tracked in
     double d_prior = 0.0;
     s = cuda_status(cudaMemcpyAsync(&d_prior, &scalars(h)->d_prior, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -680,7 +681,7 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
         A.adj_out = adj[a];
         A.adj_in = adj[a ^ 1];
         A.br = br;
-        pixvod_status r = cuda_status(cudaMemsetAsync(adj[a ^ 1], 0, R.adj_bytes, st));
+        pixvod_status r = cuda_status(cudaMemsetAsync(adj[a ^ 1], 0, adj_used, st));
         if (r != PIXVOD_OK) return r;
         if (tape) {
             h->launches++;
