@@ -21,13 +21,13 @@ __device__ __forceinline__ T ld(const void* p, size_t i) {
 // state (plane p of a tile's pixel `lane` at tile * SCR_WORDS + p * TILE_PX +
 // lane). Regions:
 //   SCR_FWD   the damped identity messages (direction k at 27 k: Lambda
-//             packed, eta), from k_adjoint_fwd, read by k_adjoint_dir;
+//             packed, eta), from k_adjoint_fwd, read by k_adjoint_check;
 //   SCR_IDF   what the reverse pass of each identity message needs from its
 //             forward (hw::IdFwd: direction k at ID_FWD_VALS k), from
 //             k_adjoint_fwd, read by k_adjoint_dir;
-//   SCR_SUM   their sums over the directions (Lambda 21, eta 6) and the sum of
-//             Lambda_k ybar(eta_k') (6), from k_adjoint_fwd, read by the main
-//             stage;
+//   SCR_SUM   the damped messages summed over the directions (Lambda 21, eta
+//             6) and the sum of Lambda_k ybar(eta_k') (6), from k_adjoint_fwd,
+//             read by the main stage;
 //   SCR_MAIN  what the main stage hands on (hw::MO_*); k_adjoint_dir adds its
 //             R and t adjoints to the MO_RB and MO_TB planes;
 //   SCR_CHK   the main stage's recomputed outputs (all but the identity
@@ -85,14 +85,12 @@ struct KernelIO {
     __device__ void identity_eta_adj(T* w) const {
         for (int q = 0; q < 6; ++q) w[q] = __ldg(scr_in + (SCR_SUM + 27 + q) * TILE_PX);
     }
-    __device__ T damped(int k, int q) const { return __ldg(scr_in + (SCR_FWD + 27 * k + q) * TILE_PX); }
     __device__ void main_out(int p, T v) const { scr_out[(SCR_MAIN + p) * TILE_PX] = v; }
     __device__ T main_in(int p) const { return __ldg(scr_in + (SCR_MAIN + p) * TILE_PX); }
-    // the recomputed update goes to the scratch and k_adjoint_check compares it
-    // with the sweep kernel's (the comparison's loads would otherwise stall the
-    // stage's chain)
-    // (the main stage's outputs only: the check forms the identity messages'
-    // itself)
+    // the main stage's recomputed outputs go to the scratch and k_adjoint_check
+    // compares them with the sweep kernel's (the comparison's loads would
+    // otherwise stall the stage's chain; the check forms the identity messages'
+    // outputs itself)
     __device__ void out(int q, T y, T scale) const {
         scr_out[(SCR_CHK + chk_plane(q)) * TILE_PX] = y;
         if (q >= 144 && (q & 1) == 0) scr_out[(SCR_CHK_S + (q - 144) / 2) * TILE_PX] = scale;
