@@ -681,18 +681,19 @@ pixvod_status backward_impl(pixvod_handle* h, const double* g_xi, const double* 
         A.adj_out = adj[a];
         A.adj_in = adj[a ^ 1];
         A.br = br;
-        pixvod_status r = cuda_status(cudaMemsetAsync(adj[a ^ 1], 0, adj_used, st));
-        if (r != PIXVOD_OK) return r;
+        pixvod_status r;
         if (tape) {
+            if ((r = cuda_status(cudaMemsetAsync(adj[a ^ 1], 0, adj_used, st))) != PIXVOD_OK) return r;
             h->launches++;
             if ((r = cuda_status(pv::launch_adjoint_sweep(A, R.slots / pv::ad::ADJ_THREADS, st))) != PIXVOD_OK)
                 return r;
         } else {
-            // rescale by a power of two: max |adj_out|, the pass, the new exponent
-            if ((r = cuda_status(cudaMemsetAsync(scale + 1, 0, sizeof(double), st))) != PIXVOD_OK) return r;
+            // rescale by a power of two: max |adj_out| (which also zeroes adj_in;
+            // scale[1] is 0 from the start of the backward or the last exponent),
+            // the pass, the new exponent
             h->launches += 2 + pv::ADJOINT_HW_LAUNCHES;  // absmax, the pass, the exponent
-            if ((r = cuda_status(pv::launch_adjoint_absmax(adj[a], adj_elems, adj64 ? 1 : 0, scale, st))) !=
-                PIXVOD_OK)
+            if ((r = cuda_status(pv::launch_adjoint_absmax(adj[a], adj[a ^ 1], adj_elems, adj64 ? 1 : 0, scale,
+                                                           st))) != PIXVOD_OK)
                 return r;
             if ((r = cuda_status(pv::launch_adjoint_hw(A, n_tiles, rw + R.off_scr, st))) != PIXVOD_OK) return r;
             if ((r = cuda_status(pv::launch_adjoint_exponent(scale, st))) != PIXVOD_OK) return r;

@@ -590,10 +590,13 @@ __device__ __forceinline__ void absmax_acc(double2 x, double& m) {
         if (isfinite(v[q]) && v[q] > m) m = v[q];
 }
 template <typename T, typename V>
-__global__ void k_adjoint_absmax(const V* __restrict__ a, size_t nv, unsigned long long* __restrict__ mx) {
+__global__ void k_adjoint_absmax(const V* __restrict__ a, V* __restrict__ z, size_t nv,
+                                 unsigned long long* __restrict__ mx) {
     T m = T(0);
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (size_t)gridDim.x * blockDim.x)
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (size_t)gridDim.x * blockDim.x) {
         absmax_acc(a[i], m);
+        z[i] = V{};
+    }
     for (int o = 16; o > 0; o >>= 1) {
         const T y = __shfl_xor_sync(0xffffffffu, m, o);
         m = y > m ? y : m;
@@ -604,6 +607,7 @@ __global__ void k_adjoint_absmax(const V* __restrict__ a, size_t nv, unsigned lo
 __global__ void k_adjoint_exponent(double* scale) {
     const double mx = scale[1];
     scale[0] += (mx > 0.0 && isfinite(mx)) ? double(ilogb(mx)) : 0.0;
+    scale[1] = 0.0;
 }
 
 }  // namespace
@@ -616,13 +620,15 @@ static int stride_blocks() {
     return (sms > 0 ? sms : 152) * 8;
 }
 
-cudaError_t launch_adjoint_absmax(const void* a, size_t n, int adj64, double* scale, cudaStream_t st) {
+cudaError_t launch_adjoint_absmax(const void* a, void* z, size_t n, int adj64, double* scale, cudaStream_t st) {
     unsigned long long* mx = reinterpret_cast<unsigned long long*>(scale + 1);
     const int blocks = stride_blocks();
     if (adj64)
-        k_adjoint_absmax<double, double2><<<blocks, 256, 0, st>>>(static_cast<const double2*>(a), n / 2, mx);
+        k_adjoint_absmax<double, double2><<<blocks, 256, 0, st>>>(static_cast<const double2*>(a),
+                                                                  static_cast<double2*>(z), n / 2, mx);
     else
-        k_adjoint_absmax<float, float4><<<blocks, 256, 0, st>>>(static_cast<const float4*>(a), n / 4, mx);
+        k_adjoint_absmax<float, float4><<<blocks, 256, 0, st>>>(static_cast<const float4*>(a),
+                                                                static_cast<float4*>(z), n / 4, mx);
     return cudaGetLastError();
 }
 

@@ -74,9 +74,11 @@ cudaError_t launch_adjoint_hw(const AdjArgs& A, int n_tiles, void* scratch, cuda
 // (adj64) or FP32
 cudaError_t launch_adjoint_seed(const AdjArgs& A, const double* grad_xi, const double* grad_invdepth, void* adj,
                                 int adj64, cudaStream_t st);
-// scale[1] = max |a[i]| over n elements (finite values; scale[1] must be 0 before)
-cudaError_t launch_adjoint_absmax(const void* a, size_t n, int adj64, double* scale, cudaStream_t st);
-// scale[0] += ilogb(scale[1]): the units of the adjoint state after a hand-written pass
+// scale[1] = max |a[i]| over n elements (finite values; scale[1] must be 0 before),
+// and z[i] = 0 over the same n elements (the next pass's adj_in)
+cudaError_t launch_adjoint_absmax(const void* a, void* z, size_t n, int adj64, double* scale, cudaStream_t st);
+// scale[0] += ilogb(scale[1]): the units of the adjoint state after a hand-written
+// pass; scale[1] = 0 again for the next pass's absmax
 cudaError_t launch_adjoint_exponent(double* scale, cudaStream_t st);
 // dL/d(sigma_D, sigma_N) from the adjoints of lam_D, 1/sigma_D and lam_N
 cudaError_t launch_sigma_grads(const double* dparam, double sigma_D, double sigma_N, double* out, cudaStream_t st);
